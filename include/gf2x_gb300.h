@@ -1,0 +1,214 @@
+/*
+ * gf2x_gb300.h -- C ABI of libgf2x_gb300.so: constant-time multiplication of
+ * dense binary polynomials (10k-60k bits and up to 131072) on an NVIDIA
+ * GB300 (sm_103a), as a full product in F2[X] or reduced modulo X^n - 1.
+ *
+ * The operation is the one of Robert & Veron, "Faster multiplication over
+ * F2[X] using AVX512 instruction set and VPCLMULQDQ instruction" (J. Crypt.
+ * Eng. 2022): Sec. 2.1 states the product (two polynomials of degree at most
+ * N-1, result of degree at most 2N-2, packed into 64-bit words), Sec. 1 maps
+ * circulant matrix-vector products of HQC/BIKE to products in
+ * F2[X]/(X^N - 1), and Sec. 2-3 (Alg. 1-3, Appendix D) give the Karatsuba
+ * and Toom-3 recursions this library runs on the GPU.
+ *
+ * Conventions for every entry point:
+ *  - Layout: a polynomial with n coefficients is ceil(n/64) little-endian
+ *    uint64 limbs; coefficient k is bit (k mod 64) of limb k/64.
+ *  - High bits: input bits at positions >= n are ignored; unused high bits
+ *    of every output limb are written as zero.
+ *  - Pointers: operand and result pointers are DEVICE pointers owned by the
+ *    caller, 8-byte aligned (16-byte alignment is faster).  An output must
+ *    not overlap either input (GF2X_EINVAL when the ranges overlap).
+ *  - Sizes: 1 <= n <= GF2X_MAX_N, else GF2X_EUNSUPPORTED.
+ *  - Asynchrony: compute calls enqueue work on `stream` (a cudaStream_t,
+ *    NULL = the legacy default stream) and return at once; argument and
+ *    plan errors are returned synchronously, launch errors as GF2X_ECUDA.
+ *  - Constant time: no branch and no memory address of the GPU code depends
+ *    on operand bits; the work done depends only on n and the plan.
+ *  - Threads: a context may be used from one host thread at a time.
+ *  - No C++ exception crosses this interface.
+ */
+#ifndef GF2X_GB300_H
+#define GF2X_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GF2X_OK = 0,
+    GF2X_EINVAL = 1,        /* bad pointer, overlap, bad flag or bad plan spec */
+    GF2X_ENOMEM = 2,        /* a context allocation failed */
+    GF2X_ECUDA = 3,         /* a CUDA runtime call failed */
+    GF2X_ETIMEOUT = 4,      /* a bounded wait ran out */
+    GF2X_EUNSUPPORTED = 5,  /* n outside [1, GF2X_MAX_N] or a plan that does not fit */
+    GF2X_EBUSY = 6,         /* resource in use (e.g. admission refused) */
+    GF2X_EDEVICE = 7        /* the checked-mode kernel reported a broken invariant */
+} gf2x_status;
+
+#define GF2X_MAX_N 131072u
+#define GF2X_MAX_LEVELS 8
+
+/* Level kinds of a recursion plan. */
+#define GF2X_LEVEL_KARATSUBA 0u  /* k-way Karatsuba split, k in {2,3,5}: Alg. 1 (KaratRec), Alg. 2 (Karat3), Alg. 3 (Karat5) */
+#define GF2X_LEVEL_TOOM3 1u      /* word-aligned Toom-3 at 0, 1, x, x+1, inf with x = X^w: Sec. 3.2 and Appendix D */
+
+/* Per-item / call flags. */
+#define GF2X_REDUCE 1u           /* result is a*b mod X^n - 1 (ceil(n/64) limbs), else the full product */
+
+/* Batch flags. */
+#define GF2X_BATCH_PERSISTENT 1u  /* grid of (SMs x resident CTAs); each CTA loops over the items */
+#define GF2X_BATCH_ITEMS_ON_DEVICE 2u /* `items` points to device memory (gf2x_item array) */
+#define GF2X_BATCH_LARGEST_FIRST 4u   /* order items by decreasing n (sizes are public) before the launch */
+
+/*
+ * A recursion plan: `nlev` split levels from the top down, then a leaf of
+ * `leaf_words` 32-bit words multiplied by a constant-time carry-less
+ * schoolbook.  Sizes follow Sec. 3.2: a Karatsuba level of child size E has
+ * parent size k*E; a Toom-3 level with word shift W (w = 32W bits) and child
+ * size E has parent size 3(E - 2W).  The top size must cover ceil(n/32)
+ * words; leaf_words = 0 picks the smallest compiled leaf that does.
+ *   kind[l]: GF2X_LEVEL_KARATSUBA (arg[l] = k) or GF2X_LEVEL_TOOM3 (arg[l] = W).
+ *   threads: CTA size (0 = chosen from the leaf count).
+ *   seq_top: 1 = the CTA multiplies the top level's children one after the
+ *            other (less shared memory, for the largest sizes).
+ */
+typedef struct {
+    uint32_t nlev;
+    uint32_t kind[GF2X_MAX_LEVELS];
+    uint32_t arg[GF2X_MAX_LEVELS];
+    uint32_t leaf_words;
+    uint32_t threads;
+    uint32_t seq_top;
+} gf2x_plan_spec;
+
+/* Facts about a plan for one n (host-side only, needs no GPU). */
+typedef struct {
+    uint32_t n;
+    uint32_t top_words;          /* padded operand size, 32-bit words */
+    uint32_t leaf_words;
+    uint32_t nleaves;            /* leaf products per multiplication */
+    uint32_t threads;
+    uint32_t smem_bytes;         /* dynamic shared memory per CTA */
+    uint32_t level_words[GF2X_MAX_LEVELS + 1]; /* operand size at each depth (top first, leaf last) */
+    uint64_t ops_full;           /* modelled 32-bit integer operations per full product */
+    uint64_t ops_leaf;           /* of which in the leaf schoolbook */
+    uint64_t clmul64;            /* 64x64-bit word products (Table tab:compKarat); leaf_words even */
+    uint64_t bytes_in;           /* HBM bytes read per product */
+    uint64_t bytes_out_full;     /* HBM bytes written, full product */
+    uint64_t bytes_out_reduced;  /* HBM bytes written, reduced product */
+} gf2x_plan_info;
+
+/* Item of a batched call.  Pointers as in the conventions above. */
+typedef struct {
+    const uint64_t *a;
+    const uint64_t *b;
+    uint64_t *out;
+    uint32_t n;
+    uint32_t flags;              /* GF2X_REDUCE or 0 */
+} gf2x_item;
+
+typedef struct gf2x_ctx gf2x_ctx;
+typedef void *gf2x_stream;       /* cudaStream_t */
+
+/* Human-readable name of a status code (static storage). */
+const char *gf2x_status_str(gf2x_status s);
+
+/* Library version string, e.g. "gf2x_gb300 1.0 sm_103a". */
+const char *gf2x_version(void);
+
+/* Default plan spec for size n (what a fresh context uses).  Host only. */
+gf2x_status gf2x_default_spec(uint32_t n, gf2x_plan_spec *spec);
+
+/* Validate `spec` for size n and describe it.  Host only, needs no GPU.
+ * GF2X_EINVAL for a malformed spec, GF2X_EUNSUPPORTED if it does not cover
+ * n or does not fit in one CTA's shared memory. */
+gf2x_status gf2x_plan_info_get(uint32_t n, const gf2x_plan_spec *spec, gf2x_plan_info *info);
+
+/* Parse a plan spec from text "T2.K3.K2.K2/8/288/0" (levels / leaf_words /
+ * threads / seq_top; the last three fields optional, 0 = automatic). */
+gf2x_status gf2x_spec_parse(const char *text, gf2x_plan_spec *spec);
+
+/* Create a context on CUDA device `device` (made current on the calling
+ * thread).  The context owns device-side plan tables and item staging
+ * buffers; it allocates nothing in the compute calls afterwards except when
+ * a batch outgrows its staging buffers. */
+gf2x_status gf2x_ctx_create(gf2x_ctx **ctx, int device);
+
+/* Release everything the context owns (waits for its work to finish). */
+void gf2x_ctx_destroy(gf2x_ctx *ctx);
+
+/* Use `spec` for every later product of size n in this context
+ * (spec = NULL restores the default).  Host-side validation only. */
+gf2x_status gf2x_ctx_set_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_plan_spec *spec);
+
+/* The spec the context currently uses for size n. */
+gf2x_status gf2x_ctx_get_plan(gf2x_ctx *ctx, uint32_t n, gf2x_plan_spec *spec);
+
+/* Enable (1) or disable (0) the checked kernels: they verify on the GPU the
+ * exactness of every division by x and x+1 and the zero padding, and record
+ * a violation for gf2x_ctx_sync_status.  Off by default. */
+gf2x_status gf2x_ctx_set_checked(gf2x_ctx *ctx, int on);
+
+/* Full product c = a*b in F2[X]: a, b have ceil(n/64) limbs, c gets
+ * ceil((2n-1)/64) limbs.  One launch of one CTA (Sec. 2.1). */
+gf2x_status gf2x_mul(gf2x_ctx *ctx, uint64_t *c, const uint64_t *a, const uint64_t *b,
+                     uint32_t n, gf2x_stream stream);
+
+/* Reduced product r = a*b mod (X^n - 1): r gets ceil(n/64) limbs
+ * (the circulant product of Sec. 1).  One launch of one CTA. */
+gf2x_status gf2x_mulmod_xn1(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a, const uint64_t *b,
+                            uint32_t n, gf2x_stream stream);
+
+/* `count` independent products of one size n in one launch.  Operand p is
+ * a + p*stride_in, result p is out + p*stride_out (strides in limbs, at
+ * least ceil(n/64) and the output size).  flags: GF2X_REDUCE, and
+ * GF2X_BATCH_PERSISTENT in batch_flags. */
+gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b,
+                             uint32_t n, size_t count, size_t stride_in, size_t stride_out,
+                             uint32_t flags, uint32_t batch_flags, gf2x_stream stream);
+
+/* `count` independent products of possibly different sizes.
+ *  - Host `items`: every item is checked, its plan resolved, and the array
+ *    copied through a pinned staging buffer of the context (a ring of four;
+ *    a reused buffer is first waited for on the host).  Items whose plans
+ *    share a leaf size run in one launch (one launch per leaf size).
+ *  - GF2X_BATCH_ITEMS_ON_DEVICE: `items` is a device array of gf2x_item read
+ *    by the kernel, which looks each plan up by n on the device; every n
+ *    must have been prepared (gf2x_ctx_prepare) and all prepared plans must
+ *    share one leaf size (else GF2X_EUNSUPPORTED).  An item whose n has no
+ *    plan is skipped and reported by gf2x_ctx_sync_status.  Nothing is
+ *    checked on the host and nothing is copied, so the call can be captured
+ *    in a CUDA graph; the array must stay valid until the work completes.
+ *  - GF2X_BATCH_PERSISTENT: a grid of (SMs x resident CTAs), each CTA
+ *    looping over items; otherwise one CTA per item.
+ *  - GF2X_BATCH_LARGEST_FIRST (host items): larger n first. */
+gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, size_t count,
+                             uint32_t batch_flags, gf2x_stream stream);
+
+/* Build and upload (synchronously on `stream`) the current plans of the
+ * given sizes, so that later calls, device-item batches and CUDA graph
+ * captures find them ready. */
+gf2x_status gf2x_ctx_prepare(gf2x_ctx *ctx, const uint32_t *sizes, size_t count, gf2x_stream stream);
+
+/* Launch shape the context uses for size n: CTA threads, dynamic shared
+ * memory, resident CTAs per SM and the SM count (any pointer may be NULL). */
+gf2x_status gf2x_ctx_launch_shape(gf2x_ctx *ctx, uint32_t n, uint32_t *threads, uint32_t *smem_bytes,
+                                  uint32_t *blocks_per_sm, uint32_t *sm_count);
+
+/* Wait for `stream`, then report and clear any checked-mode violation
+ * (GF2X_EDEVICE) or asynchronous CUDA error (GF2X_ECUDA). */
+gf2x_status gf2x_ctx_sync_status(gf2x_ctx *ctx, gf2x_stream stream);
+
+/* Text of the last error recorded in the context (static until the next
+ * call on it). */
+const char *gf2x_ctx_last_error(gf2x_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GF2X_GB300_H */

@@ -1,0 +1,632 @@
+// capi.cu -- the C ABI of include/gf2x_gb300.h: contexts, plan tables,
+// argument checks and kernel launches.  Compute happens only in the CUDA
+// kernels; there is no host fallback.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gf2x_gb300.h"
+#include "launchers.h"
+#include "plan.h"
+#include "plan_host.h"
+
+using namespace gf2x;
+
+namespace {
+
+constexpr uint32_t kPlanCapacity = 4096;  // distinct (n, spec) plans per context
+constexpr int kRing = 4;                  // item staging buffers
+
+struct PlanEntry {
+    uint32_t slot;
+    gf2x_plan_spec spec;
+};
+
+struct Staging {
+    DevItem *host = nullptr;   // pinned
+    DevItem *dev = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+};
+
+}  // namespace
+
+struct gf2x_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int checked = 0;
+    GPlan *plans_host = nullptr;   // pinned mirror, slots never change once written
+    GPlan *plans_dev = nullptr;
+    uint32_t nplans = 0;
+    std::unordered_map<uint32_t, PlanEntry> by_n;        // current plan per n
+    std::unordered_map<uint32_t, PlanEntry> by_n_checked;
+    Staging ring[kRing];
+    int ring_next = 0;
+    uint32_t *err_dev = nullptr;
+    uint32_t *plan_of_n_host = nullptr;  // pinned, GF2X_MAX_N + 1 entries
+    uint32_t *plan_of_n_dev = nullptr;
+    std::string last_error;
+    std::vector<DevItem> scratch_items;
+    std::vector<uint32_t> scratch_S;
+};
+
+static gf2x_status fail(gf2x_ctx *ctx, gf2x_status st, const std::string &msg)
+{
+    if (ctx)
+        ctx->last_error = msg;
+    return st;
+}
+
+static gf2x_status cuda_fail(gf2x_ctx *ctx, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(ctx, GF2X_ECUDA, m);
+}
+
+extern "C" const char *gf2x_status_str(gf2x_status s)
+{
+    switch (s) {
+    case GF2X_OK: return "ok";
+    case GF2X_EINVAL: return "invalid argument";
+    case GF2X_ENOMEM: return "out of memory";
+    case GF2X_ECUDA: return "CUDA error";
+    case GF2X_ETIMEOUT: return "timeout";
+    case GF2X_EUNSUPPORTED: return "unsupported size or plan";
+    case GF2X_EBUSY: return "busy";
+    case GF2X_EDEVICE: return "device invariant violated";
+    default: return "unknown status";
+    }
+}
+
+extern "C" const char *gf2x_version(void) { return "gf2x_gb300 1.0 sm_103a"; }
+
+extern "C" gf2x_status gf2x_default_spec(uint32_t n, gf2x_plan_spec *spec) { return default_spec(n, spec); }
+
+extern "C" gf2x_status gf2x_plan_info_get(uint32_t n, const gf2x_plan_spec *spec, gf2x_plan_info *info)
+{
+    if (!spec || !info)
+        return GF2X_EINVAL;
+    return build_plan(n, spec, nullptr, info);
+}
+
+extern "C" gf2x_status gf2x_spec_parse(const char *text, gf2x_plan_spec *spec) { return parse_spec(text, spec); }
+
+extern "C" gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
+{
+    if (!out)
+        return GF2X_EINVAL;
+    *out = nullptr;
+    gf2x_ctx *ctx = new (std::nothrow) gf2x_ctx();
+    if (!ctx)
+        return GF2X_ENOMEM;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return GF2X_ECUDA;
+    }
+    ctx->device = device;
+    e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&ctx->plans_host, sizeof(GPlan) * kPlanCapacity);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&ctx->plans_dev, sizeof(GPlan) * kPlanCapacity);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&ctx->err_dev, sizeof(uint32_t));
+    if (e == cudaSuccess)
+        e = cudaMemset(ctx->err_dev, 0, sizeof(uint32_t));
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&ctx->plan_of_n_host, sizeof(uint32_t) * (GF2X_MAX_N + 1));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&ctx->plan_of_n_dev, sizeof(uint32_t) * (GF2X_MAX_N + 1));
+    if (e == cudaSuccess) {
+        memset(ctx->plan_of_n_host, 0xff, sizeof(uint32_t) * (GF2X_MAX_N + 1));
+        e = cudaMemset(ctx->plan_of_n_dev, 0xff, sizeof(uint32_t) * (GF2X_MAX_N + 1));
+    }
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();
+    for (uint32_t S : kLeafSizes)
+        if (e == cudaSuccess)
+            e = preparer_for(S)(nullptr, 0, 0);
+    if (e != cudaSuccess) {
+        gf2x_ctx_destroy(ctx);
+        return GF2X_ECUDA;
+    }
+    *out = ctx;
+    return GF2X_OK;
+}
+
+extern "C" void gf2x_ctx_destroy(gf2x_ctx *ctx)
+{
+    if (!ctx)
+        return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &r : ctx->ring) {
+        if (r.host)
+            cudaFreeHost(r.host);
+        if (r.dev)
+            cudaFree(r.dev);
+        if (r.done)
+            cudaEventDestroy(r.done);
+    }
+    if (ctx->plans_host)
+        cudaFreeHost(ctx->plans_host);
+    if (ctx->plans_dev)
+        cudaFree(ctx->plans_dev);
+    if (ctx->err_dev)
+        cudaFree(ctx->err_dev);
+    if (ctx->plan_of_n_host)
+        cudaFreeHost(ctx->plan_of_n_host);
+    if (ctx->plan_of_n_dev)
+        cudaFree(ctx->plan_of_n_dev);
+    delete ctx;
+}
+
+// Build the plan for (n, spec), store it in a new slot and enqueue its upload.
+static gf2x_status install_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_plan_spec &spec, int checked,
+                                cudaStream_t stream, uint32_t *slot)
+{
+    if (ctx->nplans >= kPlanCapacity)
+        return fail(ctx, GF2X_EUNSUPPORTED, "plan table full");
+    GPlan P;
+    gf2x_status st = build_plan(n, &spec, &P, nullptr);
+    if (st != GF2X_OK)
+        return fail(ctx, st, "plan does not fit this size");
+    P.checked = checked ? 1u : 0u;
+    const uint32_t s = ctx->nplans++;
+    ctx->plans_host[s] = P;
+    cudaError_t e = cudaMemcpyAsync(ctx->plans_dev + s, ctx->plans_host + s, sizeof(GPlan), cudaMemcpyHostToDevice,
+                                    stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "plan upload");
+    *slot = s;
+    return GF2X_OK;
+}
+
+// Make `slot` the plan device-resident item batches use for n.
+static gf2x_status publish_plan(gf2x_ctx *ctx, uint32_t n, uint32_t slot, cudaStream_t stream)
+{
+    ctx->plan_of_n_host[n] = slot;
+    cudaError_t e = cudaMemcpyAsync(ctx->plan_of_n_dev + n, ctx->plan_of_n_host + n, sizeof(uint32_t),
+                                    cudaMemcpyHostToDevice, stream);
+    return e == cudaSuccess ? GF2X_OK : cuda_fail(ctx, e, "plan index upload");
+}
+
+static gf2x_status plan_for(gf2x_ctx *ctx, uint32_t n, cudaStream_t stream, uint32_t *slot)
+{
+    if (n < 1 || n > GF2X_MAX_N)
+        return fail(ctx, GF2X_EUNSUPPORTED, "n outside [1, 131072]");
+    auto &map = ctx->checked ? ctx->by_n_checked : ctx->by_n;
+    auto it = map.find(n);
+    if (it != map.end()) {
+        *slot = it->second.slot;
+        return GF2X_OK;
+    }
+    // the spec currently chosen for n (set by gf2x_ctx_set_plan or the default)
+    gf2x_plan_spec spec;
+    auto other = (ctx->checked ? ctx->by_n : ctx->by_n_checked).find(n);
+    if (other != (ctx->checked ? ctx->by_n : ctx->by_n_checked).end()) {
+        spec = other->second.spec;
+    } else {
+        gf2x_status st = default_spec(n, &spec);
+        if (st != GF2X_OK)
+            return fail(ctx, st, "no plan fits this size");
+    }
+    uint32_t s;
+    gf2x_status st = install_plan(ctx, n, spec, ctx->checked, stream, &s);
+    if (st != GF2X_OK)
+        return st;
+    map[n] = PlanEntry{s, spec};
+    *slot = s;
+    return publish_plan(ctx, n, s, stream);
+}
+
+extern "C" gf2x_status gf2x_ctx_set_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_plan_spec *spec)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    if (n < 1 || n > GF2X_MAX_N)
+        return fail(ctx, GF2X_EUNSUPPORTED, "n outside [1, 131072]");
+    cudaSetDevice(ctx->device);
+    ctx->by_n.erase(n);
+    ctx->by_n_checked.erase(n);
+    if (!spec) {
+        ctx->plan_of_n_host[n] = kNoPlan;
+        cudaMemcpy(ctx->plan_of_n_dev + n, ctx->plan_of_n_host + n, sizeof(uint32_t), cudaMemcpyHostToDevice);
+        return GF2X_OK;
+    }
+    gf2x_plan_info info;
+    gf2x_status st = build_plan(n, spec, nullptr, &info);
+    if (st != GF2X_OK)
+        return fail(ctx, st, "plan rejected for this size");
+    uint32_t s;
+    st = install_plan(ctx, n, *spec, ctx->checked, nullptr, &s);
+    if (st != GF2X_OK)
+        return st;
+    (ctx->checked ? ctx->by_n_checked : ctx->by_n)[n] = PlanEntry{s, *spec};
+    st = publish_plan(ctx, n, s, nullptr);
+    if (st != GF2X_OK)
+        return st;
+    cudaError_t e = cudaStreamSynchronize(nullptr);
+    return e == cudaSuccess ? GF2X_OK : cuda_fail(ctx, e, "plan upload");
+}
+
+extern "C" gf2x_status gf2x_ctx_get_plan(gf2x_ctx *ctx, uint32_t n, gf2x_plan_spec *spec)
+{
+    if (!ctx || !spec)
+        return GF2X_EINVAL;
+    auto &map = ctx->checked ? ctx->by_n_checked : ctx->by_n;
+    auto it = map.find(n);
+    if (it != map.end()) {
+        *spec = it->second.spec;
+        return GF2X_OK;
+    }
+    auto &o = ctx->checked ? ctx->by_n : ctx->by_n_checked;
+    auto it2 = o.find(n);
+    if (it2 != o.end()) {
+        *spec = it2->second.spec;
+        return GF2X_OK;
+    }
+    return default_spec(n, spec);
+}
+
+extern "C" gf2x_status gf2x_ctx_set_checked(gf2x_ctx *ctx, int on)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    ctx->checked = on ? 1 : 0;
+    return GF2X_OK;
+}
+
+static bool ranges_overlap(const void *p, size_t pbytes, const void *q, size_t qbytes)
+{
+    const uintptr_t a = (uintptr_t)p, b = (uintptr_t)q;
+    return a < b + qbytes && b < a + pbytes;
+}
+
+static gf2x_status check_operands(gf2x_ctx *ctx, const uint64_t *out, const uint64_t *a, const uint64_t *b,
+                                  uint32_t n, uint32_t flags, size_t count, size_t stride_in, size_t stride_out)
+{
+    if (!out || !a || !b)
+        return fail(ctx, GF2X_EINVAL, "null operand or result pointer");
+    if (((uintptr_t)out | (uintptr_t)a | (uintptr_t)b) & 7u)
+        return fail(ctx, GF2X_EINVAL, "operands and results must be 8-byte aligned");
+    if (flags & ~GF2X_REDUCE)
+        return fail(ctx, GF2X_EINVAL, "unknown flag");
+    const size_t L = (n + 63) / 64;
+    const size_t Lo = (flags & GF2X_REDUCE) ? L : (size_t)((2ull * n - 1 + 63) / 64);
+    if (count > 1 && (stride_in < L || stride_out < Lo))
+        return fail(ctx, GF2X_EINVAL, "stride smaller than the operand or result size");
+    const size_t in_bytes = 8 * ((count - 1) * stride_in + L);
+    const size_t out_bytes = 8 * ((count - 1) * stride_out + Lo);
+    if (ranges_overlap(out, out_bytes, a, in_bytes) || ranges_overlap(out, out_bytes, b, in_bytes))
+        return fail(ctx, GF2X_EINVAL, "result overlaps an operand");
+    return GF2X_OK;
+}
+
+static gf2x_status launch(gf2x_ctx *ctx, const LaunchArgs &args, uint32_t S, unsigned threads, size_t smem,
+                          size_t count, bool persistent, cudaStream_t stream)
+{
+    LaunchFn fn = launcher_for(S);
+    if (!fn)
+        return fail(ctx, GF2X_EUNSUPPORTED, "leaf size not compiled");
+    unsigned grid;
+    LaunchArgs a = args;
+    if (persistent) {
+        int per_sm = 0;
+        cudaError_t e = preparer_for(S)(&per_sm, threads, smem);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "occupancy query");
+        if (per_sm < 1)
+            return fail(ctx, GF2X_EUNSUPPORTED, "kernel does not fit on an SM");
+        grid = (unsigned)std::min<size_t>(count, (size_t)per_sm * ctx->sm_count);
+        a.persistent = 1;
+    } else {
+        if (count > 0x7fffffffu)
+            return fail(ctx, GF2X_EINVAL, "batch too large for one launch");
+        grid = (unsigned)count;
+        a.persistent = 0;
+    }
+    if (grid == 0)
+        return GF2X_OK;
+    cudaError_t e = fn(a, grid, threads, smem, stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "kernel launch");
+    return GF2X_OK;
+}
+
+static gf2x_status one_product(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n,
+                               uint32_t flags, gf2x_stream stream)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    if (n < 1 || n > GF2X_MAX_N)
+        return fail(ctx, GF2X_EUNSUPPORTED, "n outside [1, 131072]");
+    gf2x_status st = check_operands(ctx, out, a, b, n, flags, 1, 0, 0);
+    if (st != GF2X_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t slot;
+    st = plan_for(ctx, n, s, &slot);
+    if (st != GF2X_OK)
+        return st;
+    const GPlan &P = ctx->plans_host[slot];
+    LaunchArgs args;
+    memset(&args, 0, sizeof(args));
+    args.plans = ctx->plans_dev;
+    args.base = DevItem{a, b, out, slot, flags};
+    args.count = 1;
+    args.mode = kItemsSingle;
+    args.err = ctx->err_dev;
+    return launch(ctx, args, P.S, P.threads, 4ull * P.smem_words, 1, false, s);
+}
+
+extern "C" gf2x_status gf2x_mul(gf2x_ctx *ctx, uint64_t *c, const uint64_t *a, const uint64_t *b, uint32_t n,
+                                gf2x_stream stream)
+{
+    return one_product(ctx, c, a, b, n, 0u, stream);
+}
+
+extern "C" gf2x_status gf2x_mulmod_xn1(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a, const uint64_t *b,
+                                       uint32_t n, gf2x_stream stream)
+{
+    return one_product(ctx, r, a, b, n, GF2X_REDUCE, stream);
+}
+
+extern "C" gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b,
+                                        uint32_t n, size_t count, size_t stride_in, size_t stride_out,
+                                        uint32_t flags, uint32_t batch_flags, gf2x_stream stream)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    if (count == 0)
+        return GF2X_OK;
+    if (n < 1 || n > GF2X_MAX_N)
+        return fail(ctx, GF2X_EUNSUPPORTED, "n outside [1, 131072]");
+    if (batch_flags & ~(uint32_t)GF2X_BATCH_PERSISTENT)
+        return fail(ctx, GF2X_EINVAL, "unknown batch flag");
+    gf2x_status st = check_operands(ctx, out, a, b, n, flags, count, stride_in, stride_out);
+    if (st != GF2X_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t slot;
+    st = plan_for(ctx, n, s, &slot);
+    if (st != GF2X_OK)
+        return st;
+    const GPlan &P = ctx->plans_host[slot];
+    LaunchArgs args;
+    memset(&args, 0, sizeof(args));
+    args.plans = ctx->plans_dev;
+    args.base = DevItem{a, b, out, slot, flags};
+    args.stride_in = stride_in;
+    args.stride_out = stride_out;
+    args.count = (uint32_t)count;
+    args.mode = kItemsStrided;
+    args.err = ctx->err_dev;
+    if (count > 0xffffffffull)
+        return fail(ctx, GF2X_EINVAL, "batch too large");
+    return launch(ctx, args, P.S, P.threads, 4ull * P.smem_words, count,
+                  (batch_flags & GF2X_BATCH_PERSISTENT) != 0, s);
+}
+
+// Take a staging buffer of at least `count` items; waits (host) for the
+// buffer's previous copy to finish before it is reused.
+static gf2x_status take_staging(gf2x_ctx *ctx, size_t count, Staging **out)
+{
+    Staging &r = ctx->ring[ctx->ring_next];
+    ctx->ring_next = (ctx->ring_next + 1) % kRing;
+    if (r.pending) {
+        cudaError_t e = cudaEventSynchronize(r.done);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "staging wait");
+        r.pending = false;
+    }
+    if (r.cap < count) {
+        size_t cap = std::max<size_t>(count, 1024);
+        if (r.host)
+            cudaFreeHost(r.host);
+        if (r.dev)
+            cudaFree(r.dev);
+        r.host = nullptr;
+        r.dev = nullptr;
+        r.cap = 0;
+        if (cudaMallocHost((void **)&r.host, cap * sizeof(DevItem)) != cudaSuccess ||
+            cudaMalloc((void **)&r.dev, cap * sizeof(DevItem)) != cudaSuccess)
+            return fail(ctx, GF2X_ENOMEM, "staging allocation");
+        r.cap = cap;
+    }
+    if (!r.done && cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) != cudaSuccess)
+        return fail(ctx, GF2X_ECUDA, "event creation");
+    *out = &r;
+    return GF2X_OK;
+}
+
+extern "C" gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, size_t count, uint32_t batch_flags,
+                                        gf2x_stream stream)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    if (count == 0)
+        return GF2X_OK;
+    if (!items)
+        return fail(ctx, GF2X_EINVAL, "null item array");
+    if (batch_flags & ~(uint32_t)(GF2X_BATCH_PERSISTENT | GF2X_BATCH_ITEMS_ON_DEVICE | GF2X_BATCH_LARGEST_FIRST))
+        return fail(ctx, GF2X_EINVAL, "unknown batch flag");
+    if (count > 0xffffffffull)
+        return fail(ctx, GF2X_EINVAL, "batch too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool persistent = (batch_flags & GF2X_BATCH_PERSISTENT) != 0;
+    if (batch_flags & GF2X_BATCH_ITEMS_ON_DEVICE) {
+        // one launch over the caller's device array; plans are looked up by n
+        // on the device, so every size must have been prepared beforehand
+        auto &map = ctx->checked ? ctx->by_n_checked : ctx->by_n;
+        if (map.empty())
+            return fail(ctx, GF2X_EINVAL, "no prepared sizes: call gf2x_ctx_prepare first");
+        uint32_t S = 0;
+        unsigned threads = 0;
+        uint32_t smem_words = 0;
+        for (auto &kv : map) {
+            const GPlan &P = ctx->plans_host[kv.second.slot];
+            if (S && P.S != S)
+                return fail(ctx, GF2X_EUNSUPPORTED, "device item batches need one leaf size over the prepared plans");
+            S = P.S;
+            threads = std::max(threads, P.threads);
+            smem_words = std::max(smem_words, P.smem_words);
+        }
+        static_assert(sizeof(gf2x_item) == sizeof(DevItem), "gf2x_item and DevItem share a layout");
+        LaunchArgs args;
+        memset(&args, 0, sizeof(args));
+        args.plans = ctx->plans_dev;
+        args.items = reinterpret_cast<const DevItem *>(items);
+        args.count = (uint32_t)count;
+        args.mode = kItemsUser;
+        args.err = ctx->err_dev;
+        args.plan_of_n = ctx->plan_of_n_dev;
+        return launch(ctx, args, S, threads, 4ull * smem_words, count, persistent, s);
+    }
+
+    // resolve plans and check every item
+    auto &dv = ctx->scratch_items;
+    auto &Ss = ctx->scratch_S;
+    dv.resize(count);
+    Ss.resize(count);
+    for (size_t i = 0; i < count; ++i) {
+        const gf2x_item &it = items[i];
+        if (it.n < 1 || it.n > GF2X_MAX_N)
+            return fail(ctx, GF2X_EUNSUPPORTED, "item n outside [1, 131072]");
+        gf2x_status st = check_operands(ctx, it.out, it.a, it.b, it.n, it.flags, 1, 0, 0);
+        if (st != GF2X_OK)
+            return st;
+        uint32_t slot;
+        st = plan_for(ctx, it.n, s, &slot);
+        if (st != GF2X_OK)
+            return st;
+        dv[i] = DevItem{it.a, it.b, it.out, slot, it.flags};
+        Ss[i] = ctx->plans_host[slot].S;
+    }
+    // group by leaf size (one launch per group), largest n first if asked
+    std::vector<size_t> order(count);
+    for (size_t i = 0; i < count; ++i)
+        order[i] = i;
+    const bool largest_first = (batch_flags & GF2X_BATCH_LARGEST_FIRST) != 0;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        if (Ss[x] != Ss[y])
+            return Ss[x] < Ss[y];
+        if (largest_first)
+            return ctx->plans_host[dv[x].plan].n > ctx->plans_host[dv[y].plan].n;
+        return false;
+    });
+    Staging *stg;
+    gf2x_status st = take_staging(ctx, count, &stg);
+    if (st != GF2X_OK)
+        return st;
+    for (size_t i = 0; i < count; ++i)
+        stg->host[i] = dv[order[i]];
+    cudaError_t e = cudaMemcpyAsync(stg->dev, stg->host, count * sizeof(DevItem), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "item upload");
+    e = cudaEventRecord(stg->done, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "event record");
+    stg->pending = true;
+    size_t g0 = 0;
+    while (g0 < count) {
+        const uint32_t S = Ss[order[g0]];
+        size_t g1 = g0;
+        unsigned threads = 0;
+        uint32_t smem_words = 0;
+        while (g1 < count && Ss[order[g1]] == S) {
+            const GPlan &P = ctx->plans_host[dv[order[g1]].plan];
+            threads = std::max(threads, P.threads);
+            smem_words = std::max(smem_words, P.smem_words);
+            ++g1;
+        }
+        LaunchArgs args;
+        memset(&args, 0, sizeof(args));
+        args.plans = ctx->plans_dev;
+        args.items = stg->dev + g0;
+        args.count = (uint32_t)(g1 - g0);
+        args.mode = kItemsArray;
+        args.err = ctx->err_dev;
+        st = launch(ctx, args, S, threads, 4ull * smem_words, g1 - g0, persistent, s);
+        if (st != GF2X_OK)
+            return st;
+        g0 = g1;
+    }
+    return GF2X_OK;
+}
+
+extern "C" gf2x_status gf2x_ctx_sync_status(gf2x_ctx *ctx, gf2x_stream stream)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "stream synchronize");
+    uint32_t flags = 0;
+    e = cudaMemcpy(&flags, ctx->err_dev, sizeof(flags), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "error word read");
+    if (flags) {
+        cudaMemset(ctx->err_dev, 0, sizeof(uint32_t));
+        char buf[128];
+        snprintf(buf, sizeof(buf), "checked kernel reported invariant violation flags 0x%x", flags);
+        return fail(ctx, GF2X_EDEVICE, buf);
+    }
+    return GF2X_OK;
+}
+
+extern "C" const char *gf2x_ctx_last_error(gf2x_ctx *ctx)
+{
+    if (!ctx)
+        return "null context";
+    return ctx->last_error.c_str();
+}
+
+extern "C" gf2x_status gf2x_ctx_prepare(gf2x_ctx *ctx, const uint32_t *sizes, size_t count, gf2x_stream stream)
+{
+    if (!ctx || (count && !sizes))
+        return GF2X_EINVAL;
+    cudaSetDevice(ctx->device);
+    for (size_t i = 0; i < count; ++i) {
+        uint32_t slot;
+        gf2x_status st = plan_for(ctx, sizes[i], (cudaStream_t)stream, &slot);
+        if (st != GF2X_OK)
+            return st;
+    }
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    return e == cudaSuccess ? GF2X_OK : cuda_fail(ctx, e, "prepare");
+}
+
+extern "C" gf2x_status gf2x_ctx_launch_shape(gf2x_ctx *ctx, uint32_t n, uint32_t *threads, uint32_t *smem_bytes,
+                                             uint32_t *blocks_per_sm, uint32_t *sm_count)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    uint32_t slot;
+    gf2x_status st = plan_for(ctx, n, nullptr, &slot);
+    if (st != GF2X_OK)
+        return st;
+    const GPlan &P = ctx->plans_host[slot];
+    int per_sm = 0;
+    cudaError_t e = preparer_for(P.S)(&per_sm, P.threads, 4ull * P.smem_words);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "occupancy query");
+    if (threads)
+        *threads = P.threads;
+    if (smem_bytes)
+        *smem_bytes = 4u * P.smem_words;
+    if (blocks_per_sm)
+        *blocks_per_sm = (uint32_t)per_sm;
+    if (sm_count)
+        *sm_count = (uint32_t)ctx->sm_count;
+    return GF2X_OK;
+}

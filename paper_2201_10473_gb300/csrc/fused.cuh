@@ -1,0 +1,484 @@
+// fused.cuh -- one CTA multiplies one pair of binary polynomials entirely
+// in shared memory: stage -> evaluate (Toom-3 / Karatsuba, breadth first)
+// -> leaf products -> interpolate (bottom up) -> fold mod X^n - 1 -> store.
+//
+// Constant time: every loop bound, branch and shared/global address below
+// depends only on the plan (n, sizes) and on thread indices, never on
+// operand bits.  Operand bits only flow through XOR/AND/shift data paths.
+#pragma once
+#include <stdint.h>
+
+#include "plan.h"
+
+namespace gf2x {
+
+__device__ __forceinline__ uint32_t fdiv(const FastDiv &f, uint32_t x)
+{
+    return f.m ? __umulhi(x, f.m) : x;
+}
+
+// ---------------------------------------------------------------- leaf
+// S x S-word carry-less product by the comb method: for every bit position
+// j (high to low) of the 32-bit words of B, shift the accumulator left by one
+// and XOR A into word i of it wherever bit j of B[i] is set (AND with the
+// sign-extended bit: no branch).  32 (S^2 + 4S) integer ops for a product of
+// (32S)^2 bit pairs.  This replaces the paper's Mult64 (Sec. 2.1, PCLMULQDQ),
+// which the GPU does not have.
+template <int S>
+__device__ __forceinline__ void leaf_comb(uint32_t *slot)
+{
+    uint32_t a[S], b[S], c[2 * S];
+#pragma unroll
+    for (int i = 0; i < S; i += 2) {
+        const uint2 ta = *reinterpret_cast<const uint2 *>(slot + i);
+        const uint2 tb = *reinterpret_cast<const uint2 *>(slot + S + i);
+        a[i] = ta.x;
+        a[i + 1] = ta.y;
+        b[i] = tb.x;
+        b[i + 1] = tb.y;
+    }
+#pragma unroll
+    for (int i = 0; i < 2 * S; ++i)
+        c[i] = 0u;
+#pragma unroll 2
+    for (int j = 0; j < 32; ++j) {
+#pragma unroll
+        for (int k = 2 * S - 1; k > 0; --k)
+            c[k] = __funnelshift_l(c[k - 1], c[k], 1);
+        c[0] <<= 1;
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            const uint32_t m = (uint32_t)((int32_t)b[i] >> 31);
+            b[i] <<= 1;
+#pragma unroll
+            for (int k = 0; k < S; ++k)
+                c[i + k] ^= a[k] & m;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2 * S; i += 2)
+        *reinterpret_cast<uint2 *>(slot + i) = make_uint2(c[i], c[i + 1]);
+}
+
+template <int S>
+__device__ __forceinline__ void leaf_pass(uint32_t *base, uint32_t nleaf)
+{
+    for (uint32_t l = threadIdx.x; l < nleaf; l += blockDim.x)
+        leaf_comb<S>(base + l * (2u * S));
+}
+
+// ---------------------------------------------------------------- staging
+// Words 0..T0-1 of an operand: the caller's ceil(n/64) limbs read as 32-bit
+// words, bits >= n cleared, zero padding up to the plan size.
+__device__ __forceinline__ void stage_operand(uint32_t *dst, const uint64_t *src, const GPlan &P)
+{
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
+    const uint32_t L32 = P.L32, T0 = P.T0, r = P.n & 31u;
+    for (uint32_t w = threadIdx.x; w < T0; w += blockDim.x) {
+        uint32_t v = 0u;
+        if (w < L32) {
+            v = __ldg(s32 + w);
+            if (w == L32 - 1 && r)
+                v &= (1u << r) - 1u;
+        }
+        dst[w] = v;
+    }
+}
+
+// ---------------------------------------------------------------- evaluation
+// Children c_begin .. c_begin+c_count-1 (numbered over all parents of the
+// pass) of one level: operand word e of child j of parent p.
+__device__ __forceinline__ void eval_level(const GLevel &L, const uint32_t *__restrict__ par,
+                                           uint32_t *__restrict__ ch, uint32_t c_begin, uint32_t c_count)
+{
+    const uint32_t E = L.E, twoE = 2u * E, T = L.T;
+    const uint32_t total = c_count * twoE;
+    for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const uint32_t cl = fdiv(L.div2E, idx);
+        const uint32_t r = idx - cl * twoE;
+        const uint32_t c = c_begin + cl;
+        const uint32_t p = fdiv(L.divnch, c);
+        const uint32_t j = c - p * L.nch;
+        const uint32_t half = r >= E ? 1u : 0u;
+        const uint32_t e = r - half * E;
+        const uint32_t *X = par + p * (2u * T) + half * T;
+        uint32_t v;
+        if (L.kind == kKaratsuba) {
+            // Alg. 1-3: child j multiplies A_i (single) or A_i + A_j (pair)
+            const uint32_t s0 = L.sel[j][0], s1 = L.sel[j][1];
+            v = X[s0 * E + e];
+            if (s1 != 255u)
+                v ^= X[s1 * E + e];
+        } else {
+            // Appendix D evaluation at 0, 1, x, x+1, inf, x = X^w (word shift W)
+            const uint32_t np = L.np, W = L.W;
+            const bool in = e < np;
+            const uint32_t a0 = in ? X[e] : 0u;
+            const uint32_t a1 = in ? X[np + e] : 0u;
+            const uint32_t a2 = in ? X[2u * np + e] : 0u;
+            const uint32_t a1x = (e >= W && e - W < np) ? X[np + e - W] : 0u;          // a1 * x
+            const uint32_t a2x = (e >= 2u * W && e - 2u * W < np) ? X[2u * np + e - 2u * W] : 0u;  // a2 * x^2
+            switch (j) {
+            case 0: v = a0; break;                              // C(0)
+            case 1: v = a0 ^ a1 ^ a2; break;                    // C(1)
+            case 2: v = a0 ^ a1x ^ a2x; break;                  // C(x)
+            case 3: v = a0 ^ a1 ^ a2 ^ a1x ^ a2x; break;        // C(x+1)
+            default: v = a2; break;                             // C(inf)
+            }
+        }
+        ch[cl * twoE + r] = v;
+    }
+}
+
+// ---------------------------------------------------------------- interpolation
+// k-way Karatsuba reconstruction: word q of the parent product is the XOR of
+// term_p[q - pE] for the (at most two) positions p covering q.
+__device__ __forceinline__ void interp_karatsuba(const GLevel &L, const uint32_t *__restrict__ ch,
+                                                 uint32_t *__restrict__ par, uint32_t npar)
+{
+    const uint32_t E = L.E, twoE = 2u * E, twoT = 2u * L.T, k = L.k;
+    const uint32_t total = npar * twoT;
+    for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const uint32_t p = fdiv(L.div2T, idx);
+        const uint32_t q = idx - p * twoT;
+        const uint32_t *R = ch + p * L.nch * twoE;
+        const uint32_t hi = fdiv(L.divE, q);
+        uint32_t v = 0u;
+#pragma unroll
+        for (uint32_t u = 0; u < 2; ++u) {
+            if (hi < u)
+                continue;
+            const uint32_t pos = hi - u;
+            if (pos > 2u * k - 2u)
+                continue;
+            const uint32_t x = q - pos * E;
+            const uint32_t nt = L.nterms[pos];
+            for (uint32_t t = 0; t < nt; ++t)
+                v ^= R[L.terms[pos][t] * twoE + x];
+        }
+        par[idx] = v;
+    }
+}
+
+// In-place prefix XOR over W-word blocks (division by x+1 = X^w + 1, Sec. 3.2:
+// the quotient is the product with sum_i X^{wi}, i.e. Q[i] = P[i] ^ Q[i-W]),
+// for nseg segments `stride` words apart, each `len` words long.  Three
+// passes: chunk totals, exclusive scan of the totals, chunk rescans.
+static __device__ void scan_xor_blocks(uint32_t *base, uint32_t nseg, uint32_t stride, uint32_t len, uint32_t W,
+                                uint32_t *part, uint32_t part_words)
+{
+    const uint32_t rows = (len + W - 1) / W;
+    uint32_t nchunk = part_words / (nseg * W);
+    nchunk = nchunk < 1u ? 1u : (nchunk > 32u ? 32u : nchunk);
+    if (nchunk > rows)
+        nchunk = rows;
+    const uint32_t rpc = (rows + nchunk - 1) / nchunk;
+    const uint32_t per_seg = W * nchunk;
+    const uint32_t ntask = nseg * per_seg;
+    for (uint32_t t = threadIdx.x; t < ntask; t += blockDim.x) {
+        const uint32_t seg = t / per_seg, rem = t - seg * per_seg, c = rem / W, col = rem - c * W;
+        const uint32_t *a = base + seg * stride;
+        const uint32_t r0 = c * rpc, r1 = min(rows, r0 + rpc);
+        uint32_t acc = 0u;
+        for (uint32_t r = r0; r < r1; ++r) {
+            const uint32_t i = r * W + col;
+            if (i < len)
+                acc ^= a[i];
+        }
+        part[t] = acc;
+    }
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < nseg * W; s += blockDim.x) {
+        const uint32_t seg = s / W, col = s - seg * W;
+        uint32_t run = 0u;
+        for (uint32_t c = 0; c < nchunk; ++c) {
+            const uint32_t t = seg * per_seg + c * W + col;
+            const uint32_t v = part[t];
+            part[t] = run;
+            run ^= v;
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < ntask; t += blockDim.x) {
+        const uint32_t seg = t / per_seg, rem = t - seg * per_seg, c = rem / W, col = rem - c * W;
+        uint32_t *a = base + seg * stride;
+        const uint32_t r0 = c * rpc, r1 = min(rows, r0 + rpc);
+        uint32_t acc = part[t];
+        for (uint32_t r = r0; r < r1; ++r) {
+            const uint32_t i = r * W + col;
+            if (i < len) {
+                acc ^= a[i];
+                a[i] = acc;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void flag_error(uint32_t *err, uint32_t code)
+{
+    if (err)
+        atomicOr(err, code);
+}
+
+// Toom-3 interpolation (Appendix D), as the sequence
+//   c3 = ((v0+v1+vx+vx1)/x)/(x+1)
+//   c2 = ((vx+v0)/x + c3 x^2 + c4 x^3 + v1 + v0 + c3 + c4)/(x+1)
+//   c1 = v1 + v0 + c2 + c3 + c4,   c0 = v0,  c4 = v_inf
+// (two word shifts and two prefix-XOR scans; it reproduces the rows of
+// M^-1), then C = sum_i c_i X^{32 n' i}.
+static __device__ void interp_toom3(const GPlan &P, const GLevel &L, const uint32_t *__restrict__ ch,
+                             uint32_t *__restrict__ par, uint32_t *tmp, uint32_t *part, uint32_t npar,
+                             uint32_t *err)
+{
+    const uint32_t E = L.E, twoE = 2u * E, W = L.W, np = L.np, twonp = 2u * np;
+    const uint32_t len = P.checked ? twoE - W : twonp;  // words of c3, c2 computed
+    const uint32_t tstride = 4u * E;                     // per parent: c3 at [0,2E), c2 at [2E,4E)
+    // (1) t = (v0 + v1 + vx + vx1) / x
+    for (uint32_t idx = threadIdx.x; idx < npar * len; idx += blockDim.x) {
+        const uint32_t p = idx / len, x = idx - p * len;
+        const uint32_t *R = ch + p * 5u * twoE;
+        tmp[p * tstride + x] = R[x + W] ^ R[twoE + x + W] ^ R[2u * twoE + x + W] ^ R[3u * twoE + x + W];
+    }
+    if (P.checked) {
+        for (uint32_t idx = threadIdx.x; idx < npar * W; idx += blockDim.x) {
+            const uint32_t p = idx / W, x = idx - p * W;
+            const uint32_t *R = ch + p * 5u * twoE;
+            if ((R[x] ^ R[twoE + x] ^ R[2u * twoE + x] ^ R[3u * twoE + x]) | (R[2u * twoE + x] ^ R[x]))
+                flag_error(err, kErrDivX);
+        }
+    }
+    __syncthreads();
+    // (2) c3 = t / (x+1)
+    scan_xor_blocks(tmp, npar, tstride, len, W, part, P.part_words);
+    // (3) numerator of c2
+    for (uint32_t idx = threadIdx.x; idx < npar * len; idx += blockDim.x) {
+        const uint32_t p = idx / len, x = idx - p * len;
+        const uint32_t *R = ch + p * 5u * twoE;
+        const uint32_t *c3 = tmp + p * tstride;
+        const uint32_t *c4 = R + 4u * twoE;
+        uint32_t v = R[2u * twoE + x + W] ^ R[x + W];          // (vx + v0) / x
+        if (x >= 2u * W)
+            v ^= c3[x - 2u * W];                                // c3 x^2
+        if (x >= 3u * W)
+            v ^= c4[x - 3u * W];                                // c4 x^3
+        v ^= R[twoE + x] ^ R[x] ^ c3[x] ^ c4[x];                // v1 + v0 + c3 + c4
+        tmp[p * tstride + twoE + x] = v;
+    }
+    if (P.checked) {
+        for (uint32_t idx = threadIdx.x; idx < npar * (len - twonp); idx += blockDim.x) {
+            const uint32_t p = idx / (len - twonp), x = twonp + idx % (len - twonp);
+            if (tmp[p * tstride + x])
+                flag_error(err, kErrDivX1);
+        }
+    }
+    __syncthreads();
+    // (4) c2 = numerator / (x+1)
+    scan_xor_blocks(tmp + twoE, npar, tstride, len, W, part, P.part_words);
+    if (P.checked) {
+        for (uint32_t idx = threadIdx.x; idx < npar * (len - twonp); idx += blockDim.x) {
+            const uint32_t p = idx / (len - twonp), x = twonp + idx % (len - twonp);
+            if (tmp[p * tstride + twoE + x])
+                flag_error(err, kErrDivX1);
+        }
+    }
+    // (5) recomposition C = c0 + c1 X^n' + c2 X^2n' + c3 X^3n' + c4 X^4n'
+    const uint32_t twoT = 2u * L.T;  // = 6 n'
+    for (uint32_t idx = threadIdx.x; idx < npar * twoT; idx += blockDim.x) {
+        const uint32_t p = idx / twoT, q = idx - p * twoT;
+        const uint32_t *R = ch + p * 5u * twoE;
+        const uint32_t *c3 = tmp + p * tstride;
+        const uint32_t *c2 = c3 + twoE;
+        uint32_t v = 0u;
+#pragma unroll
+        for (uint32_t i = 0; i < 5; ++i) {
+            if (q < i * np)
+                continue;
+            const uint32_t y = q - i * np;
+            if (y >= twonp)
+                continue;
+            switch (i) {
+            case 0: v ^= R[y]; break;
+            case 1: v ^= R[twoE + y] ^ R[y] ^ c3[y] ^ R[4u * twoE + y] ^ c2[y]; break;
+            case 2: v ^= c2[y]; break;
+            case 3: v ^= c3[y]; break;
+            default: v ^= R[4u * twoE + y]; break;
+            }
+        }
+        par[idx] = v;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void interp_level(const GPlan &P, const GLevel &L, const uint32_t *ch, uint32_t *par,
+                                             uint32_t *sm, uint32_t npar, uint32_t *err)
+{
+    if (L.kind == kKaratsuba) {
+        interp_karatsuba(L, ch, par, npar);
+        __syncthreads();
+    } else {
+        interp_toom3(P, L, ch, par, sm + P.tmp_off, sm + P.part_off, npar, err);
+    }
+}
+
+// ---------------------------------------------------------------- epilogue
+// Full product: the first ceil((2n-1)/64) limbs.  Reduced product:
+// r = (c mod X^n) + (c >> n), since X^n = 1 in F2[X]/(X^n - 1) and deg c <= 2n-2
+// (Sec. 1, circulant isomorphism).
+__device__ __forceinline__ void epilogue(const GPlan &P, const DevItem &it, const uint32_t *C, uint32_t *err)
+{
+    uint32_t *o32 = reinterpret_cast<uint32_t *>(it.out);
+    const uint32_t twoT = 2u * P.T0;
+    if (it.flags & 1u) {
+        const uint32_t nw = 2u * P.L64, sh = P.n >> 5, s = P.n & 31u, L32 = P.L32;
+        for (uint32_t q = threadIdx.x; q < nw; q += blockDim.x) {
+            const uint32_t lo = q < twoT ? C[q] : 0u;
+            const uint32_t i0 = q + sh;
+            const uint32_t h0 = i0 < twoT ? C[i0] : 0u;
+            const uint32_t h1 = i0 + 1u < twoT ? C[i0 + 1u] : 0u;
+            const uint32_t f = __funnelshift_r(h0, h1, s);
+            uint32_t v = lo ^ f;
+            if (q >= L32)
+                v = 0u;
+            else if (q == L32 - 1 && s)
+                v &= (1u << s) - 1u;
+            o32[q] = v;
+        }
+    } else {
+        const uint32_t nw = 2u * P.Lfull64;
+        for (uint32_t q = threadIdx.x; q < nw; q += blockDim.x)
+            o32[q] = q < twoT ? C[q] : 0u;
+    }
+    if (P.checked) {
+        const uint32_t top = 2u * P.n - 1u;  // first bit that must be zero
+        for (uint32_t q = (top >> 5) + threadIdx.x; q < twoT; q += blockDim.x) {
+            const uint32_t mask = (q == (top >> 5)) ? ~((1u << (top & 31u)) - 1u) : ~0u;
+            if (C[q] & mask)
+                flag_error(err, kErrPad);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- one product
+template <int S>
+__device__ void run_product(const GPlan &P, const DevItem &it, uint32_t *sm, uint32_t *err)
+{
+    uint32_t *top = sm + P.top_off;
+    stage_operand(top, it.a, P);
+    stage_operand(top + P.T0, it.b, P);
+    __syncthreads();
+    const uint32_t nlev = P.nlev;
+    if (nlev == 0) {
+        if (threadIdx.x == 0)
+            leaf_comb<S>(top);
+        __syncthreads();
+    } else if (!P.seq_top) {
+        for (uint32_t l = 0; l < nlev; ++l) {
+            const GLevel &L = P.lev[l];
+            eval_level(L, sm + L.in_off, sm + L.ch_off, 0u, L.npar * L.nch);
+            __syncthreads();
+        }
+        leaf_pass<S>(sm + P.lev[nlev - 1].ch_off, P.nleaf_pass);
+        __syncthreads();
+        for (int l = (int)nlev - 1; l >= 0; --l) {
+            const GLevel &L = P.lev[l];
+            interp_level(P, L, sm + L.ch_off, sm + L.in_off, sm, L.npar, err);
+        }
+    } else {
+        const GLevel &L0 = P.lev[0];
+        const uint32_t twoE0 = 2u * L0.E;
+        for (uint32_t j = 0; j < L0.nch; ++j) {
+            eval_level(L0, sm + L0.in_off, sm + L0.ch_off, j, 1u);
+            __syncthreads();
+            for (uint32_t l = 1; l < nlev; ++l) {
+                const GLevel &L = P.lev[l];
+                eval_level(L, sm + L.in_off, sm + L.ch_off, 0u, L.npar * L.nch);
+                __syncthreads();
+            }
+            leaf_pass<S>(sm + P.lev[nlev - 1].ch_off, P.nleaf_pass);
+            __syncthreads();
+            for (int l = (int)nlev - 1; l >= 1; --l) {
+                const GLevel &L = P.lev[l];
+                interp_level(P, L, sm + L.ch_off, sm + L.in_off, sm, L.npar, err);
+            }
+            const uint32_t *src = sm + L0.ch_off;
+            uint32_t *dst = sm + P.prod_off + j * twoE0;
+            for (uint32_t w = threadIdx.x; w < twoE0; w += blockDim.x)
+                dst[w] = src[w];
+            __syncthreads();
+        }
+        interp_level(P, L0, sm + P.prod_off, sm + L0.in_off, sm, 1u, err);
+    }
+    epilogue(P, it, top, err);
+}
+
+__device__ __forceinline__ DevItem fetch_item(const LaunchArgs &args, uint32_t i)
+{
+    if (args.mode == kItemsArray)
+        return args.items[i];
+    if (args.mode == kItemsUser) {
+        DevItem it = args.items[i];
+        it.plan = it.plan <= 131072u ? __ldg(args.plan_of_n + it.plan) : kNoPlan;
+        return it;
+    }
+    DevItem it = args.base;
+    if (args.mode == kItemsStrided) {
+        it.a += (uint64_t)i * args.stride_in;
+        it.b += (uint64_t)i * args.stride_in;
+        it.out += (uint64_t)i * args.stride_out;
+    }
+    return it;
+}
+
+template <int S>
+struct LeafTraits {
+    static constexpr int kMaxThreads = S <= 12 ? 768 : 512;
+};
+
+template <int S>
+__global__ void __launch_bounds__(LeafTraits<S>::kMaxThreads, 1)
+fused_mul_kernel(const LaunchArgs args)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ GPlan P;
+    const uint32_t step = args.persistent ? gridDim.x : args.count;
+    for (uint32_t i = blockIdx.x; i < args.count; i += step) {
+        const DevItem it = fetch_item(args, i);
+        if (it.plan == kNoPlan) {  // uniform over the CTA: every thread read the same item
+            if (threadIdx.x == 0)
+                flag_error(args.err, kErrNoPlan);
+            continue;
+        }
+        __syncthreads();
+        {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(args.plans + it.plan);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
+            for (uint32_t w = threadIdx.x; w < sizeof(GPlan) / 4; w += blockDim.x)
+                dst[w] = __ldg(src + w);
+        }
+        __syncthreads();
+        run_product<S>(P, it, sm, args.err);
+    }
+}
+
+// Host launcher, one instantiation per compiled leaf size.
+template <int S>
+cudaError_t launch_fused(const LaunchArgs &args, unsigned grid, unsigned block, size_t smem, cudaStream_t stream)
+{
+    fused_mul_kernel<S><<<grid, block, smem, stream>>>(args);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t prepare_fused(int *max_blocks_per_sm, unsigned block, size_t smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(fused_mul_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         232448 - (int)sizeof(GPlan) - 256);
+    if (e != cudaSuccess)
+        return e;
+    if (max_blocks_per_sm)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, fused_mul_kernel<S>, (int)block, smem);
+    return e;
+}
+
+}  // namespace gf2x

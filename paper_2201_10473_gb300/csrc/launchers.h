@@ -1,0 +1,47 @@
+// launchers.h -- per-leaf-size entry points of the fused kernel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace gf2x {
+#define GF2X_DECLARE_LEAF(S)                                                                              \
+    cudaError_t launch_fused_s##S(const LaunchArgs &a, unsigned g, unsigned b, size_t sm, cudaStream_t st); \
+    cudaError_t prepare_fused_s##S(int *blocks, unsigned b, size_t sm);
+GF2X_DECLARE_LEAF(4)
+GF2X_DECLARE_LEAF(6)
+GF2X_DECLARE_LEAF(8)
+GF2X_DECLARE_LEAF(10)
+GF2X_DECLARE_LEAF(12)
+GF2X_DECLARE_LEAF(16)
+#undef GF2X_DECLARE_LEAF
+
+typedef cudaError_t (*LaunchFn)(const LaunchArgs &, unsigned, unsigned, size_t, cudaStream_t);
+typedef cudaError_t (*PrepareFn)(int *, unsigned, size_t);
+
+// launcher for leaf size S (null if not compiled)
+inline LaunchFn launcher_for(uint32_t S)
+{
+    switch (S) {
+    case 4: return launch_fused_s4;
+    case 6: return launch_fused_s6;
+    case 8: return launch_fused_s8;
+    case 10: return launch_fused_s10;
+    case 12: return launch_fused_s12;
+    case 16: return launch_fused_s16;
+    default: return nullptr;
+    }
+}
+inline PrepareFn preparer_for(uint32_t S)
+{
+    switch (S) {
+    case 4: return prepare_fused_s4;
+    case 6: return prepare_fused_s6;
+    case 8: return prepare_fused_s8;
+    case 10: return prepare_fused_s10;
+    case 12: return prepare_fused_s12;
+    case 16: return prepare_fused_s16;
+    default: return nullptr;
+    }
+}
+}  // namespace gf2x

@@ -1,0 +1,11 @@
+// Instantiates the fused multiplication kernel for a leaf of 12 32-bit words.
+#include "fused.cuh"
+#include "launchers.h"
+
+namespace gf2x {
+cudaError_t launch_fused_s12(const LaunchArgs &a, unsigned g, unsigned b, size_t sm, cudaStream_t st)
+{
+    return launch_fused<12>(a, g, b, sm, st);
+}
+cudaError_t prepare_fused_s12(int *blocks, unsigned b, size_t sm) { return prepare_fused<12>(blocks, b, sm); }
+}  // namespace gf2x

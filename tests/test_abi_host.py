@@ -1,0 +1,147 @@
+"""Host-side checks of libgf2x_gb300.so: it loads, exports every symbol the
+header declares, and its plan algebra reproduces the paper's sizes.  No GPU."""
+import json
+import os
+import re
+
+import pytest
+
+from paper_2201_10473_gb300 import build as pbuild
+from paper_2201_10473_gb300 import gf2x
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+CONFIG_SIZES = [12323, 17669, 24659, 35851, 40973, 57637]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pbuild.build()
+
+
+def declared_functions():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(gf2x_[a-z0-9_]+)\s*\(", text,
+                                re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_functions()
+    assert len(names) >= 15
+    L = gf2x.lib()
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_status_strings_and_version():
+    L = gf2x.lib()
+    assert L.gf2x_status_str(0) == b"ok"
+    assert b"sm_103a" in L.gf2x_version()
+    for s in range(8):
+        assert L.gf2x_status_str(s)
+
+
+def _chains(elem):
+    """Karatsuba chains (leaf S, levels) whose top size is exactly `elem` words."""
+    for S in (16, 12, 10, 8, 6, 4):
+        if elem % S:
+            continue
+        r = elem // S
+        for lead in (1, 3, 5):
+            if r % lead:
+                continue
+            r2 = r // lead
+            if r2 & (r2 - 1) == 0:
+                yield S, ([f"K{lead}"] if lead > 1 else []) + ["K2"] * (r2.bit_length() - 1)
+
+
+def test_paper_sizes_through_the_abi():
+    """The library's planner reproduces every printed size (Sec. 3.2 size rule)."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_plan_sizes.json")))
+    checked = 0
+    for case in g["cases"]:
+        n = case["bits"]
+        if len(case["levels"]) > 1 or n > 80000:
+            continue  # two Toom levels, or too large for one CTA: sizes checked in test_plan_algebra
+        elem = case["elem_bits"] // 32
+        info = None
+        for S, chain in _chains(elem):
+            if len(chain) + 1 > gf2x.MAX_LEVELS:
+                continue
+            for seq in (0, 1):
+                try:
+                    info = gf2x.plan_info(n, ".".join(case["levels"] + chain) + f"/{S}/0/{seq}")
+                    break
+                except gf2x.Gf2xError:
+                    pass
+            if info:
+                break
+        assert info is not None, case
+        assert 32 * info["top_words"] == case["bits"], (case, info)
+        assert info["level_words"][1] == elem
+        checked += 1
+    assert checked >= 13
+
+
+@pytest.mark.parametrize("n", CONFIG_SIZES + [1, 2, 63, 64, 65, 1000, 4096, 65536])
+def test_default_plan_covers_n_and_fits(n):
+    spec = gf2x.default_spec(n)
+    info = gf2x.plan_info(n, spec)
+    assert 32 * info["top_words"] >= n
+    assert info["smem_bytes"] <= 232448
+    assert info["threads"] % 32 == 0 and 128 <= info["threads"] <= 1024
+    assert info["ops_leaf"] <= info["ops_full"]
+
+
+def test_clmul_counts_table_compkarat_through_abi():
+    for r in range(1, 6):
+        t = 2 ** r
+        for lead, mult in ((None, 1), (3, 6), (5, 15)):
+            chain = ([f"K{lead}"] if lead else []) + ["K2"] * r
+            spec = ".".join(chain) + "/4"
+            words = 4 * (lead or 1) * t
+            info = gf2x.plan_info(32 * words, spec)
+            # 4-word leaves are 2x2 64-bit schoolbooks: 4 clmul64 each
+            assert info["clmul64"] == 4 * mult * 3 ** r
+
+
+def test_spec_parse_roundtrip_and_errors():
+    s = gf2x.parse_spec("T2.K3.K2.K2/8/288/0")
+    assert gf2x.spec_text(s) == "T2.K3.K2.K2/8/288/0"
+    for bad in ["K4/8", "X2", "T0", "K2/7", "K2/8/100", "K2/8/0/1", "K2/8/0/0/9"]:
+        with pytest.raises(gf2x.Gf2xError):
+            gf2x.parse_spec(bad)
+
+
+def test_plan_rejections():
+    with pytest.raises(gf2x.Gf2xError) as e:
+        gf2x.plan_info(17669, "K2/8")           # does not cover n
+    assert e.value.status == 5
+    with pytest.raises(gf2x.Gf2xError):
+        gf2x.plan_info(0, "K2/8")
+    with pytest.raises(gf2x.Gf2xError):
+        gf2x.plan_info(131073, "K2/8")
+    with pytest.raises(gf2x.Gf2xError):
+        gf2x.plan_info(57637, "K5.K3.K2.K2.K2/16/0/0")  # breadth-first does not fit shared memory
+
+
+def test_seq_top_reduces_shared_memory():
+    with pytest.raises(gf2x.Gf2xError):
+        gf2x.plan_info(57637, "T16.K5.K2.K2.K2.K2/8/0/0")   # breadth first: too much shared memory
+    seq = gf2x.plan_info(57637, "T16.K5.K2.K2.K2.K2/8/0/1")
+    assert seq["smem_bytes"] <= 232448
+    assert 32 * seq["top_words"] == 58368
+
+
+def test_paper_hqc_plans_through_the_abi():
+    """tab:NRperfs: hqc-128 at 18048 bits (Toom3Karat3, w=64) and hqc-256 at
+    58368 bits (Toom3Karat5, w=512)."""
+    a = gf2x.plan_info(17669, "T2.K3.K2.K2.K2/8")
+    assert 32 * a["top_words"] == 18048 and a["nleaves"] == 5 * 6 * 27
+    b = gf2x.plan_info(57637, "T16.K5.K2.K2.K2.K2/8/0/1")
+    assert 32 * b["top_words"] == 58368 and b["nleaves"] == 5 * 15 * 81
