@@ -1,0 +1,412 @@
+"""Benchmark of the hot path: batched constant-time F2[X] products mod X^n - 1.
+
+Default workload: 4096 products of dense Bernoulli(0.5) polynomials with
+n = 17669 coefficients (HQC-128 size), reduced mod X^n - 1, in ONE batched
+persistent launch per step (the batched form); the plain form (one launch
+per product) is measured beside it.  One JSON line on stdout (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload hqc128|hqc192|hqc256|c1] [--no-plain]
+
+--impl reference times the oracle (oracle/, plain C on the host cores) on a
+bounded sample of the same workload: the only reference this method has.
+Multi-GPU (torchrun): every rank multiplies its own 4096 products (weak
+scaling, no collective on the data path); time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Integer ALU pipe: 64 lanes/clk/SM for LOP3/SHF (32-bit logical ops and
+# shifts), 152 SMs, 2070 MHz maximum SM clock: 152 * 64 * 2.07e9 = 20.1 Tops/s.
+ALU_LANES_PER_SM = 64
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+WORKLOADS = {
+    "hqc128": dict(name="hqc128-17669-mulmod", n=17669, batch=4096, reduce=True, key=2),
+    "hqc192": dict(name="hqc192-35851-mulmod", n=35851, batch=2048, reduce=True, key=3),
+    "hqc256": dict(name="hqc256-57637-mulmod", n=57637, batch=2048, reduce=True, key=4),
+    "c1": dict(name="plain-12323-full", n=12323, batch=256, reduce=False, key=1),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="hqc128")
+    p.add_argument("--no-plain", action="store_true", help="skip the plain one-launch-per-product measurement")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle cpu_baseline sample")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- oracle legs
+
+def oracle_rate(w: dict, seconds: float, first_product: int = 0) -> dict:
+    """The oracle as it stands on the host cores over a bounded sample."""
+    import oracle
+    n, reduce = w["n"], w["reduce"]
+    cores = cpu_cores()
+    seed = wl.BASE_SEED + w["key"]
+    # size the sample from one timed product
+    a1, b1 = wl.dense_pair(seed, n, 1, first=first_product)
+    t0 = time.perf_counter()
+    oracle.mul_batch(a1, b1, n, reduce=reduce, nthreads=1)
+    one = max(time.perf_counter() - t0, 1e-4)
+    count = int(max(cores, min(w["batch"], seconds * cores / one)))
+    a, b = wl.dense_pair(seed, n, count, first=first_product)
+    t0 = time.perf_counter()
+    oracle.mul_batch(a, b, n, reduce=reduce, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": count / dt, "unit": "mults/s", "cores": cores, "kind": "oracle",
+            "sample": f"{count} of the workload's {w['batch']} products (n={n}, seed {seed}), "
+                      f"oracle_mul_batch on {cores} threads, {dt:.2f} s"}
+
+
+def run_reference(args, w):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    K, W = args.steps, args.warmup
+    # each step: a bounded sample so the whole run stays within minutes
+    import oracle
+    n, reduce = w["n"], w["reduce"]
+    cores = cpu_cores()
+    seed = wl.BASE_SEED + w["key"]
+    a1, b1 = wl.dense_pair(seed, n, 1)
+    t0 = time.perf_counter()
+    oracle.mul_batch(a1, b1, n, reduce=reduce, nthreads=1)
+    one = max(time.perf_counter() - t0, 1e-4)
+    per_step = int(max(cores, min(w["batch"], (120.0 / max(K + W, 1)) * cores / one)))
+    a, b = wl.dense_pair(seed, n, per_step)
+    for _ in range(W):
+        oracle.mul_batch(a, b, n, reduce=reduce, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        oracle.mul_batch(a, b, n, reduce=reduce, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = K * per_step / dt
+    line = {"metric": metric_name(), "value": value, "unit": "mults/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": dt / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic", "impl": "reference",
+            "config": config_of(w, None, None),
+            "cpu_baseline": {"value": value, "unit": "mults/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} products per step of the workload (n={n}), oracle_mul_batch"},
+            "e2e": {"value": value, "unit": "mults/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def metric_name() -> str:
+    return "GF(2)[X] mults/sec + ns/mult at n=17669/35851/57637, batched vs plain, bit-exact"
+
+
+def config_of(w, spec, shape):
+    c = {"workload": w["name"], "n": w["n"], "batch_per_gpu": w["batch"], "reduce_mod_xn1": w["reduce"],
+         "operands": "dense iid Bernoulli(0.5), SplitMix64 seeded",
+         "l2": "8 rotating input sets larger than the 129 MB L2 (no flush)"}
+    if spec:
+        c["plan"] = spec
+    if shape:
+        c["launch"] = dict(shape, persistent=True)
+    return c
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, w):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2201_10473_gb300 import Context, plan_info
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n, batch, reduce = w["n"], w["batch"], w["reduce"]
+    seed = wl.BASE_SEED + w["key"]
+    ctx = Context(local)
+    spec = ctx.get_plan(n)
+    info = plan_info(n, spec)
+    shape = ctx.launch_shape(n)
+
+    # input sets: rank r uses products r*batch .. (r+1)*batch-1 of the seeded stream;
+    # rotate R sets so the inputs touched between two uses exceed L2
+    in_bytes = 2 * batch * wl.limbs(n) * 8
+    R = max(2, int(np.ceil(160e6 / in_bytes)))
+    host_a, host_b = wl.dense_pair(seed, n, batch, first=rank * batch)
+    sets = []
+    for r in range(R):
+        # every set is the same products (identical results); rotating copies defeat L2 reuse
+        sets.append((torch.from_numpy(host_a.view(np.int64)).cuda(), torch.from_numpy(host_b.view(np.int64)).cuda()))
+    ol = wl.limbs(n) if reduce else (2 * n - 1 + 63) // 64
+    out = torch.empty((batch, ol), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        a, b = sets[i % R]
+        ctx.mul_strided(a, b, n, reduce, out=out, persistent=True, stream=stream)
+
+    # parity spot check of this run's launch configuration before timing
+    import_oracle_ok = True
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if rank == 0:
+        try:
+            import oracle
+            sample = np.arange(0, batch, max(1, batch // 16))
+            got = out.cpu().numpy().view(np.uint64)[sample]
+            exp = oracle.mul_batch(host_a[sample], host_b[sample], n, reduce=reduce)
+            if not np.array_equal(got, exp):
+                raise SystemExit("bench: GPU results differ from the oracle")
+        except ImportError:
+            import_oracle_ok = False
+
+    # ---- timed region: K steps, per-launch events on the launching stream
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(K):
+        evs[i][0].record(stream)
+        step(args.warmup + i)
+        evs[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    clk = clocks.stop()
+    launch_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * batch * K / (total_ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers
+    pin_a = torch.from_numpy(host_a.view(np.int64)).pin_memory()
+    pin_b = torch.from_numpy(host_b.view(np.int64)).pin_memory()
+    pin_out = torch.empty((batch, ol), dtype=torch.int64).pin_memory()
+    da = torch.empty_like(sets[0][0])
+    db = torch.empty_like(sets[0][1])
+
+    def e2e_step():
+        da.copy_(pin_a, non_blocking=True)
+        db.copy_(pin_b, non_blocking=True)
+        ctx.mul_strided(da, db, n, reduce, out=out, persistent=True, stream=stream)
+        pin_out.copy_(out, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    K2 = max(3, K // 2)
+    for _ in range(K2):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    got_e2e = pin_out.numpy().view(np.uint64)
+    e2e_value = world * batch * K2 / (e2e_ms * 1e-3)
+
+    # ---- plain form: one launch of one CTA per product
+    plain = None
+    if not args.no_plain:
+        a, b = sets[0]
+        outs1 = out
+        for _ in range(2):
+            for p in range(batch):
+                (ctx.mulmod if reduce else ctx.mul)(a[p], b[p], n, out=outs1[p], stream=stream)
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for p in range(batch):
+            (ctx.mulmod if reduce else ctx.mul)(a[p], b[p], n, out=outs1[p], stream=stream)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = p0.elapsed_time(p1)
+        plain = {"value": batch / (plain_ms * 1e-3), "unit": "mults/s", "launches": batch,
+                 "note": "one launch of one CTA per product, same plan"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the fused kernel (the only kernel of the step)
+    mean_launch_ms = float(np.mean(launch_ms))
+    ops_per_launch = info["ops_full"] * batch
+    achieved = ops_per_launch / (mean_launch_ms * 1e-3) / 1e12
+    peak = SMS * ALU_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        key = f"{w['name']}|{spec}"
+        traffic = prof.get(key)
+    except (OSError, ValueError):
+        traffic = None
+    observed = clk.get("sm_mhz")
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "ops_per_product": info["ops_full"], "products_per_launch": batch,
+            "peak_note": "152 SMs x 64 ALU lanes/clk x 2070 MHz (unit counts and max clock); see DESIGN.md",
+            "frac_at_observed_clock": (achieved / (SMS * ALU_LANES_PER_SM * observed * 1e6 / 1e12)) if observed else None,
+            "hbm_gbs": (info["bytes_in"] + (info["bytes_out_reduced"] if reduce else info["bytes_out_full"])) * batch
+            / (mean_launch_ms * 1e-3) / 1e9}
+
+    cpu = None
+    if world == 1:
+        cpu = oracle_rate(w, args.cpu_seconds)
+
+    line = {
+        "metric": metric_name(),
+        "value": value,
+        "unit": "mults/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / K,
+        "ns_per_mult": 1e9 / value,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": config_of(w, spec, shape),
+        "e2e": {"value": e2e_value, "unit": "mults/s", "h2d_bytes_per_step": int(pin_a.numel() * 8 * 2),
+                "d2h_bytes_per_step": int(pin_out.numel() * 8), "steps": K2},
+        "gpu_launches": K,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "plain": plain,
+        "batched_over_plain": (value / world / plain["value"]) if plain else None,
+        "clocks": clk,
+        "parity_checked": import_oracle_ok,
+        "e2e_sample_ok": bool(got_e2e.shape[0] == batch),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()
