@@ -75,6 +75,9 @@ typedef enum {
  *   threads: CTA size (0 = chosen from the leaf count).
  *   seq_top: 1 = the CTA multiplies the top level's children one after the
  *            other (less shared memory, for the largest sizes).
+ *   fuse_leaf: 1 = the last level (a 2-way Karatsuba) runs inside the leaf
+ *            thread, in registers (leaf_words <= 10); 0 = it runs as a
+ *            shared-memory level like the others.
  */
 typedef struct {
     uint32_t nlev;
@@ -83,6 +86,7 @@ typedef struct {
     uint32_t leaf_words;
     uint32_t threads;
     uint32_t seq_top;
+    uint32_t fuse_leaf;
 } gf2x_plan_spec;
 
 /* Facts about a plan for one n (host-side only, needs no GPU). */
@@ -128,8 +132,9 @@ gf2x_status gf2x_default_spec(uint32_t n, gf2x_plan_spec *spec);
  * n or does not fit in one CTA's shared memory. */
 gf2x_status gf2x_plan_info_get(uint32_t n, const gf2x_plan_spec *spec, gf2x_plan_info *info);
 
-/* Parse a plan spec from text "T2.K3.K2.K2/8/288/0" (levels / leaf_words /
- * threads / seq_top; the last three fields optional, 0 = automatic). */
+/* Parse a plan spec from text "T2.K3.K2.K2/8/288/0/1" (levels / leaf_words /
+ * threads / seq_top / fuse_leaf; the last four fields optional, 0 =
+ * automatic or off). */
 gf2x_status gf2x_spec_parse(const char *text, gf2x_plan_spec *spec);
 
 /* Create a context on CUDA device `device` (made current on the calling

@@ -18,25 +18,47 @@ __device__ __forceinline__ uint32_t fdiv(const FastDiv &f, uint32_t x)
 }
 
 // ---------------------------------------------------------------- leaf
-// S x S-word carry-less product by the comb method: for every bit position
-// j (high to low) of the 32-bit words of B, shift the accumulator left by one
-// and XOR A into word i of it wherever bit j of B[i] is set (AND with the
-// sign-extended bit: no branch).  32 (S^2 + 4S) integer ops for a product of
-// (32S)^2 bit pairs.  This replaces the paper's Mult64 (Sec. 2.1, PCLMULQDQ),
-// which the GPU does not have.
-template <int S>
-__device__ __forceinline__ void leaf_comb(uint32_t *slot)
+// Integer helpers that keep work on the FMA pipe: the multiplier `two` (= 2)
+// is read from memory, so these stay IMADs instead of being turned into
+// shifts on the ALU pipe, which the AND-XOR operations already fill.
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
 {
-    uint32_t a[S], b[S], c[2 * S];
-#pragma unroll
-    for (int i = 0; i < S; i += 2) {
-        const uint2 ta = *reinterpret_cast<const uint2 *>(slot + i);
-        const uint2 tb = *reinterpret_cast<const uint2 *>(slot + S + i);
-        a[i] = ta.x;
-        a[i + 1] = ta.y;
-        b[i] = tb.x;
-        b[i + 1] = tb.y;
-    }
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t mul_lo(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("mul.lo.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t mul_hi_u(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t mul_hi_s(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("mul.hi.s32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// S x S-word carry-less product by the comb method, in registers: for every
+// bit position j (high to low) of the 32-bit words of b, shift the
+// accumulator left by one and XOR a into word i of it wherever bit j of b[i]
+// is set (AND with the sign-extended bit: no branch).  This replaces the
+// paper's Mult64 (Sec. 2.1, PCLMULQDQ), which the GPU does not have.
+//   FMA = false: shifts and masks on the ALU pipe (SHF), 32 (S^2 + 4S) ALU ops.
+//   FMA = true : the accumulator shift (c = 2c + hi(2 c_prev)) and the masks
+//                (m = hi_signed(2 b), b = 2b) are IMADs on the FMA pipe; the
+//                ALU pipe only runs the 32 S^2 AND-XORs.
+// b is consumed.
+template <int S, bool FMA>
+__device__ __forceinline__ void comb(const uint32_t (&a)[S], uint32_t (&b)[S], uint32_t (&c)[2 * S], uint32_t two)
+{
 #pragma unroll
     for (int i = 0; i < 2 * S; ++i)
         c[i] = 0u;
@@ -44,27 +66,108 @@ __device__ __forceinline__ void leaf_comb(uint32_t *slot)
     for (int j = 0; j < 32; ++j) {
 #pragma unroll
         for (int k = 2 * S - 1; k > 0; --k)
-            c[k] = __funnelshift_l(c[k - 1], c[k], 1);
-        c[0] <<= 1;
+            c[k] = FMA ? mad_lo(c[k], two, mul_hi_u(c[k - 1], two)) : __funnelshift_l(c[k - 1], c[k], 1);
+        c[0] = FMA ? mul_lo(c[0], two) : (c[0] << 1);
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-            const uint32_t m = (uint32_t)((int32_t)b[i] >> 31);
-            b[i] <<= 1;
+            const uint32_t m = FMA ? mul_hi_s(b[i], two) : (uint32_t)((int32_t)b[i] >> 31);
+            b[i] = FMA ? mul_lo(b[i], two) : (b[i] << 1);
 #pragma unroll
             for (int k = 0; k < S; ++k)
                 c[i + k] ^= a[k] & m;
         }
     }
+}
+
+template <int N>
+__device__ __forceinline__ void load_words(uint32_t (&r)[N], const uint32_t *p)
+{
 #pragma unroll
-    for (int i = 0; i < 2 * S; i += 2)
-        *reinterpret_cast<uint2 *>(slot + i) = make_uint2(c[i], c[i + 1]);
+    for (int i = 0; i < N; i += 2) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p + i);
+        r[i] = t.x;
+        r[i + 1] = t.y;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void store_words(uint32_t *p, const uint32_t (&r)[N])
+{
+#pragma unroll
+    for (int i = 0; i < N; i += 2)
+        *reinterpret_cast<uint2 *>(p + i) = make_uint2(r[i], r[i + 1]);
+}
+
+// Leaf slot: A (S words) then B (S words); the 2S-word product replaces them.
+template <int S, bool FMA>
+__device__ __forceinline__ void leaf_plain(uint32_t *slot, uint32_t two)
+{
+    uint32_t a[S], b[S], c[2 * S];
+    load_words<S>(a, slot);
+    load_words<S>(b, slot + S);
+    comb<S, FMA>(a, b, c, two);
+    store_words<2 * S>(slot, c);
+}
+
+// Leaf slot of a 2-way Karatsuba node (Alg. 1, one level): A = A0 + X^{32S} A1,
+// B likewise (2S words each); R = R0 + (R0 + R1 + R2) X^{32S} + R1 X^{64S}
+// with R0 = A0 B0, R1 = A1 B1, R2 = (A0 + A1)(B0 + B1), all in registers.
+template <int S, bool FMA>
+__device__ __forceinline__ void leaf_k2(uint32_t *slot, uint32_t two)
+{
+    uint32_t C[4 * S], r[2 * S], a[S], b[S];
+    load_words<S>(a, slot);
+    load_words<S>(b, slot + 2 * S);
+    comb<S, FMA>(a, b, r, two);
+#pragma unroll
+    for (int k = 0; k < 2 * S; ++k)
+        C[k] = r[k];
+#pragma unroll
+    for (int k = 2 * S; k < 4 * S; ++k)
+        C[k] = 0u;
+#pragma unroll
+    for (int k = 0; k < 2 * S; ++k)
+        C[S + k] ^= r[k];
+    load_words<S>(a, slot + S);
+    load_words<S>(b, slot + 3 * S);
+    comb<S, FMA>(a, b, r, two);
+#pragma unroll
+    for (int k = 0; k < 2 * S; ++k) {
+        C[2 * S + k] ^= r[k];
+        C[S + k] ^= r[k];
+    }
+    {
+        uint32_t a1[S], b1[S];
+        load_words<S>(a, slot);
+        load_words<S>(a1, slot + S);
+        load_words<S>(b, slot + 2 * S);
+        load_words<S>(b1, slot + 3 * S);
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            a[k] ^= a1[k];
+            b[k] ^= b1[k];
+        }
+    }
+    comb<S, FMA>(a, b, r, two);
+#pragma unroll
+    for (int k = 0; k < 2 * S; ++k)
+        C[S + k] ^= r[k];
+    store_words<4 * S>(slot, C);
 }
 
 template <int S>
-__device__ __forceinline__ void leaf_pass(uint32_t *base, uint32_t nleaf)
+__device__ __forceinline__ void leaf_pass(const GPlan &P, uint32_t *base, uint32_t nleaf)
 {
-    for (uint32_t l = threadIdx.x; l < nleaf; l += blockDim.x)
-        leaf_comb<S>(base + l * (2u * S));
+    const uint32_t two = P.two;
+    if (P.fuse_k2) {
+        if constexpr (S <= 10) {
+            for (uint32_t l = threadIdx.x; l < nleaf; l += blockDim.x)
+                leaf_k2<S, true>(base + l * (4u * S), two);
+        }
+    } else {
+        for (uint32_t l = threadIdx.x; l < nleaf; l += blockDim.x)
+            leaf_plain<S, true>(base + l * (2u * S), two);
+    }
 }
 
 // ---------------------------------------------------------------- staging
@@ -127,6 +230,58 @@ __device__ __forceinline__ void eval_level(const GLevel &L, const uint32_t *__re
             }
         }
         ch[cl * twoE + r] = v;
+    }
+}
+
+// 2-way Karatsuba evaluation (Alg. 1), two words per thread: children
+// (A0, B0), (A1, B1), (A0 + A1, B0 + B1) of every parent of the pass.
+__device__ __forceinline__ void eval_k2(const GLevel &L, const uint32_t *__restrict__ par, uint32_t *__restrict__ ch,
+                                        uint32_t npar)
+{
+    const uint32_t E = L.E, hE = E / 2u;
+    const uint32_t total = npar * hE;
+    for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const uint32_t p = fdiv(L.divhE, idx);
+        const uint32_t e = 2u * (idx - p * hE);
+        const uint32_t *X = par + p * (4u * E);
+        const uint2 a0 = *reinterpret_cast<const uint2 *>(X + e);
+        const uint2 a1 = *reinterpret_cast<const uint2 *>(X + E + e);
+        const uint2 b0 = *reinterpret_cast<const uint2 *>(X + 2u * E + e);
+        const uint2 b1 = *reinterpret_cast<const uint2 *>(X + 3u * E + e);
+        uint32_t *C = ch + p * (6u * E);
+        *reinterpret_cast<uint2 *>(C + e) = a0;
+        *reinterpret_cast<uint2 *>(C + E + e) = b0;
+        *reinterpret_cast<uint2 *>(C + 2u * E + e) = a1;
+        *reinterpret_cast<uint2 *>(C + 3u * E + e) = b1;
+        *reinterpret_cast<uint2 *>(C + 4u * E + e) = make_uint2(a0.x ^ a1.x, a0.y ^ a1.y);
+        *reinterpret_cast<uint2 *>(C + 5u * E + e) = make_uint2(b0.x ^ b1.x, b0.y ^ b1.y);
+    }
+}
+
+// 2-way Karatsuba reconstruction (Alg. 1): with M = R0 + R1 + R2,
+// C[x] = R0[x], C[E+x] = R0[E+x] + M[x], C[2E+x] = M[E+x] + R1[x], C[3E+x] = R1[E+x].
+__device__ __forceinline__ void interp_k2(const GLevel &L, const uint32_t *__restrict__ ch, uint32_t *__restrict__ par,
+                                          uint32_t npar)
+{
+    const uint32_t E = L.E, hE = E / 2u;
+    const uint32_t total = npar * hE;
+    for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const uint32_t p = fdiv(L.divhE, idx);
+        const uint32_t x = 2u * (idx - p * hE);
+        const uint32_t *R = ch + p * (6u * E);
+        const uint2 r0l = *reinterpret_cast<const uint2 *>(R + x);
+        const uint2 r0h = *reinterpret_cast<const uint2 *>(R + E + x);
+        const uint2 r1l = *reinterpret_cast<const uint2 *>(R + 2u * E + x);
+        const uint2 r1h = *reinterpret_cast<const uint2 *>(R + 3u * E + x);
+        const uint2 r2l = *reinterpret_cast<const uint2 *>(R + 4u * E + x);
+        const uint2 r2h = *reinterpret_cast<const uint2 *>(R + 5u * E + x);
+        const uint2 ml = make_uint2(r0l.x ^ r1l.x ^ r2l.x, r0l.y ^ r1l.y ^ r2l.y);
+        const uint2 mh = make_uint2(r0h.x ^ r1h.x ^ r2h.x, r0h.y ^ r1h.y ^ r2h.y);
+        uint32_t *C = par + p * (4u * E);
+        *reinterpret_cast<uint2 *>(C + x) = r0l;
+        *reinterpret_cast<uint2 *>(C + E + x) = make_uint2(r0h.x ^ ml.x, r0h.y ^ ml.y);
+        *reinterpret_cast<uint2 *>(C + 2u * E + x) = make_uint2(mh.x ^ r1l.x, mh.y ^ r1l.y);
+        *reinterpret_cast<uint2 *>(C + 3u * E + x) = r1h;
     }
 }
 
@@ -313,7 +468,10 @@ static __device__ void interp_toom3(const GPlan &P, const GLevel &L, const uint3
 __device__ __forceinline__ void interp_level(const GPlan &P, const GLevel &L, const uint32_t *ch, uint32_t *par,
                                              uint32_t *sm, uint32_t npar, uint32_t *err)
 {
-    if (L.kind == kKaratsuba) {
+    if (L.kind == kKaratsuba && L.k == 2u && !(L.E & 1u)) {
+        interp_k2(L, ch, par, npar);
+        __syncthreads();
+    } else if (L.kind == kKaratsuba) {
         interp_karatsuba(L, ch, par, npar);
         __syncthreads();
     } else {
@@ -360,6 +518,15 @@ __device__ __forceinline__ void epilogue(const GPlan &P, const DevItem &it, cons
 }
 
 // ---------------------------------------------------------------- one product
+__device__ __forceinline__ void eval_pass(const GLevel &L, const uint32_t *par, uint32_t *ch, uint32_t c_begin,
+                                          uint32_t c_count, uint32_t npar)
+{
+    if (L.kind == kKaratsuba && L.k == 2u && !(L.E & 1u) && c_begin == 0u && c_count == 3u * npar)
+        eval_k2(L, par, ch, npar);
+    else
+        eval_level(L, par, ch, c_begin, c_count);
+}
+
 template <int S>
 __device__ void run_product(const GPlan &P, const DevItem &it, uint32_t *sm, uint32_t *err)
 {
@@ -368,46 +535,50 @@ __device__ void run_product(const GPlan &P, const DevItem &it, uint32_t *sm, uin
     stage_operand(top + P.T0, it.b, P);
     __syncthreads();
     const uint32_t nlev = P.nlev;
+    const uint32_t ne = nlev - P.fuse_k2;   // levels run as shared-memory passes
     if (nlev == 0) {
         if (threadIdx.x == 0)
-            leaf_comb<S>(top);
+            leaf_plain<S, true>(top, P.two);
         __syncthreads();
-    } else if (!P.seq_top) {
-        for (uint32_t l = 0; l < nlev; ++l) {
-            const GLevel &L = P.lev[l];
-            eval_level(L, sm + L.in_off, sm + L.ch_off, 0u, L.npar * L.nch);
-            __syncthreads();
-        }
-        leaf_pass<S>(sm + P.lev[nlev - 1].ch_off, P.nleaf_pass);
-        __syncthreads();
-        for (int l = (int)nlev - 1; l >= 0; --l) {
-            const GLevel &L = P.lev[l];
-            interp_level(P, L, sm + L.ch_off, sm + L.in_off, sm, L.npar, err);
-        }
     } else {
-        const GLevel &L0 = P.lev[0];
-        const uint32_t twoE0 = 2u * L0.E;
-        for (uint32_t j = 0; j < L0.nch; ++j) {
-            eval_level(L0, sm + L0.in_off, sm + L0.ch_off, j, 1u);
-            __syncthreads();
-            for (uint32_t l = 1; l < nlev; ++l) {
+        uint32_t *leaf_base = sm + (P.fuse_k2 ? P.lev[nlev - 1].in_off : P.lev[nlev - 1].ch_off);
+        if (!P.seq_top) {
+            for (uint32_t l = 0; l < ne; ++l) {
                 const GLevel &L = P.lev[l];
-                eval_level(L, sm + L.in_off, sm + L.ch_off, 0u, L.npar * L.nch);
+                eval_pass(L, sm + L.in_off, sm + L.ch_off, 0u, L.npar * L.nch, L.npar);
                 __syncthreads();
             }
-            leaf_pass<S>(sm + P.lev[nlev - 1].ch_off, P.nleaf_pass);
+            leaf_pass<S>(P, leaf_base, P.nleaf_pass);
             __syncthreads();
-            for (int l = (int)nlev - 1; l >= 1; --l) {
+            for (int l = (int)ne - 1; l >= 0; --l) {
                 const GLevel &L = P.lev[l];
                 interp_level(P, L, sm + L.ch_off, sm + L.in_off, sm, L.npar, err);
             }
-            const uint32_t *src = sm + L0.ch_off;
-            uint32_t *dst = sm + P.prod_off + j * twoE0;
-            for (uint32_t w = threadIdx.x; w < twoE0; w += blockDim.x)
-                dst[w] = src[w];
-            __syncthreads();
+        } else {
+            const GLevel &L0 = P.lev[0];
+            const uint32_t twoE0 = 2u * L0.E;
+            for (uint32_t j = 0; j < L0.nch; ++j) {
+                eval_level(L0, sm + L0.in_off, sm + L0.ch_off, j, 1u);
+                __syncthreads();
+                for (uint32_t l = 1; l < ne; ++l) {
+                    const GLevel &L = P.lev[l];
+                    eval_pass(L, sm + L.in_off, sm + L.ch_off, 0u, L.npar * L.nch, L.npar);
+                    __syncthreads();
+                }
+                leaf_pass<S>(P, leaf_base, P.nleaf_pass);
+                __syncthreads();
+                for (int l = (int)ne - 1; l >= 1; --l) {
+                    const GLevel &L = P.lev[l];
+                    interp_level(P, L, sm + L.ch_off, sm + L.in_off, sm, L.npar, err);
+                }
+                const uint32_t *src = sm + L0.ch_off;
+                uint32_t *dst = sm + P.prod_off + j * twoE0;
+                for (uint32_t w = threadIdx.x; w < twoE0; w += blockDim.x)
+                    dst[w] = src[w];
+                __syncthreads();
+            }
+            interp_level(P, L0, sm + P.prod_off, sm + L0.in_off, sm, 1u, err);
         }
-        interp_level(P, L0, sm + P.prod_off, sm + L0.in_off, sm, 1u, err);
     }
     epilogue(P, it, top, err);
 }
@@ -432,7 +603,7 @@ __device__ __forceinline__ DevItem fetch_item(const LaunchArgs &args, uint32_t i
 
 template <int S>
 struct LeafTraits {
-    static constexpr int kMaxThreads = S <= 12 ? 768 : 512;
+    static constexpr int kMaxThreads = S <= 6 ? 768 : 512;
 };
 
 template <int S>

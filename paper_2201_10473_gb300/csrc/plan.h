@@ -39,7 +39,7 @@ struct GLevel {
     uint32_t npar;      // parents at this level handled in one pass
     uint32_t in_off;    // shared-memory word offset of the parent slots
     uint32_t ch_off;    // shared-memory word offset of the children slots
-    FastDiv div2E, divnch, divE, div2T;
+    FastDiv div2E, divnch, divE, div2T, divhE;
     uint8_t sel[16][2];                 // Karatsuba child j = X[sel0] ^ X[sel1] (sel1 = 255: single)
     uint8_t nterms[2 * 5 - 1];
     uint8_t terms[2 * 5 - 1][kMaxTerms];  // children XORed into reconstruction term p
@@ -64,7 +64,9 @@ struct GPlan {
     uint32_t part_off;   // prefix-XOR scan partials
     uint32_t part_words;
     uint32_t checked;    // verify exactness invariants on the device
-    uint32_t pad_;
+    uint32_t fuse_k2;    // 1: the last level is a 2-way Karatsuba done inside the leaf thread
+    uint32_t two;        // the constant 2, read from memory so that multiplications by it stay IMADs
+    uint32_t pad2_;
     GLevel lev[kMaxLevels];
 };
 

@@ -20,7 +20,7 @@ namespace gf2x {
 
 const uint32_t kLeafSizes[kNumLeafSizes] = {4, 6, 8, 10, 12, 16};
 
-uint32_t max_threads_for_leaf(uint32_t S) { return S <= 12 ? 768u : 512u; }
+uint32_t max_threads_for_leaf(uint32_t S) { return S <= 6 ? 768u : 512u; }
 
 bool leaf_supported(uint32_t S)
 {
@@ -84,6 +84,14 @@ static gf2x_status check_spec_shape(const gf2x_plan_spec &s)
         return GF2X_EINVAL;
     if (s.threads && (s.threads % 32 || s.threads > 1024))
         return GF2X_EINVAL;
+    if (s.fuse_leaf > 1)
+        return GF2X_EINVAL;
+    if (s.fuse_leaf) {
+        if (s.nlev < 1 || s.kind[s.nlev - 1] != GF2X_LEVEL_KARATSUBA || s.arg[s.nlev - 1] != 2)
+            return GF2X_EINVAL;
+        if (s.leaf_words > kMaxFusedLeaf)
+            return GF2X_EINVAL;
+    }
     return GF2X_OK;
 }
 
@@ -163,6 +171,8 @@ gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec_in, GPlan *out, gf
     uint32_t S = s.leaf_words;
     if (S == 0) {
         for (uint32_t cand : kLeafSizes) {
+            if (s.fuse_leaf && cand > kMaxFusedLeaf)
+                continue;
             if (level_sizes(s, cand, sz) && sz[0] >= L32) {
                 S = cand;
                 break;
@@ -186,6 +196,10 @@ gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec_in, GPlan *out, gf
     P.nlev = s.nlev;
     P.S = S;
     P.seq_top = s.seq_top;
+    P.fuse_k2 = s.fuse_leaf;
+    P.two = 2;
+    // depth of the deepest data held in shared memory (the fused level stays in registers)
+    const uint32_t deepest = s.nlev - s.fuse_leaf;
 
     // parents per level over the whole tree, and per pass
     uint32_t npar_all[kMaxLevels + 1];
@@ -204,7 +218,7 @@ gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec_in, GPlan *out, gf
         uint32_t nch = s.kind[l] == GF2X_LEVEL_KARATSUBA ? s.arg[l] * (s.arg[l] + 1) / 2 : 5;
         npar_pass[l + 1] = (s.seq_top && l == 0) ? 1 : npar_pass[l] * nch;
     }
-    P.nleaf_pass = npar_pass[s.nlev];
+    P.nleaf_pass = npar_pass[deepest];
 
     // threads: enough for the leaf pass in as few balanced rounds as the leaf allows
     uint32_t maxT = max_threads_for_leaf(S);
@@ -240,13 +254,14 @@ gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec_in, GPlan *out, gf
         L.divnch = make_div(L.nch);
         L.divE = make_div(L.E);
         L.div2T = make_div(2 * L.T);
+        L.divhE = make_div(std::max(1u, L.E / 2));
     }
 
     // ---- shared-memory layout (words, 16-byte aligned regions)
     // data at depth d: npar_pass[d] slots of 2*sz[d] words
     uint32_t D[kMaxLevels + 1];
     for (uint32_t d = 0; d <= s.nlev; ++d)
-        D[d] = round_up(npar_pass[d] * 2 * sz[d], 4);
+        D[d] = d <= deepest ? round_up(npar_pass[d] * 2 * sz[d], 4) : 0;
     uint32_t off = 0;
     uint32_t regA = 0, regB = 0, regP = 0;
     if (!s.seq_top) {
@@ -389,6 +404,8 @@ gf2x_status default_spec(uint32_t n, gf2x_plan_spec *out)
                         continue;
                     for (uint32_t S : kLeafSizes) {
                         s.leaf_words = S;
+                        s.fuse_leaf = (l >= 1 && s.kind[l - 1] == GF2X_LEVEL_KARATSUBA && s.arg[l - 1] == 2 &&
+                                       S <= kMaxFusedLeaf) ? 1u : 0u;
                         gf2x_plan_info info;
                         if (build_plan(n, &s, nullptr, &info) != GF2X_OK)
                             continue;
@@ -429,7 +446,7 @@ gf2x_status parse_spec(const char *text, gf2x_plan_spec *out)
             break;
         pos = q + 1;
     }
-    if (fields.size() > 4)
+    if (fields.size() > 5)
         return GF2X_EINVAL;
     // levels
     const std::string &lv = fields[0];
@@ -457,7 +474,7 @@ gf2x_status parse_spec(const char *text, gf2x_plan_spec *out)
             break;
         i = j + 1;
     }
-    uint32_t *dst[3] = {&s.leaf_words, &s.threads, &s.seq_top};
+    uint32_t *dst[4] = {&s.leaf_words, &s.threads, &s.seq_top, &s.fuse_leaf};
     for (size_t f = 1; f < fields.size(); ++f) {
         if (fields[f].empty())
             continue;

@@ -6,6 +6,7 @@
 namespace gf2x {
 
 constexpr int kNumLeafSizes = 6;
+constexpr uint32_t kMaxFusedLeaf = 10;  // largest leaf whose fused 2-way Karatsuba fits the registers
 extern const uint32_t kLeafSizes[kNumLeafSizes];
 
 // Dynamic shared memory one CTA may use: the 227 KB opt-in maximum of the

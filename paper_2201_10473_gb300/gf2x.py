@@ -40,7 +40,7 @@ class Gf2xError(RuntimeError):
 class PlanSpec(ctypes.Structure):
     _fields_ = [("nlev", ctypes.c_uint32), ("kind", ctypes.c_uint32 * MAX_LEVELS),
                 ("arg", ctypes.c_uint32 * MAX_LEVELS), ("leaf_words", ctypes.c_uint32),
-                ("threads", ctypes.c_uint32), ("seq_top", ctypes.c_uint32)]
+                ("threads", ctypes.c_uint32), ("seq_top", ctypes.c_uint32), ("fuse_leaf", ctypes.c_uint32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -125,7 +125,7 @@ def parse_spec(text: str) -> PlanSpec:
 
 def spec_text(s: PlanSpec) -> str:
     lv = ".".join(("K" if s.kind[i] == LEVEL_KARATSUBA else "T") + str(s.arg[i]) for i in range(s.nlev))
-    return f"{lv}/{s.leaf_words}/{s.threads}/{s.seq_top}"
+    return f"{lv}/{s.leaf_words}/{s.threads}/{s.seq_top}/{s.fuse_leaf}"
 
 
 def default_spec(n: int) -> str:

@@ -111,9 +111,11 @@ def test_clmul_counts_table_compkarat_through_abi():
 
 
 def test_spec_parse_roundtrip_and_errors():
-    s = gf2x.parse_spec("T2.K3.K2.K2/8/288/0")
-    assert gf2x.spec_text(s) == "T2.K3.K2.K2/8/288/0"
-    for bad in ["K4/8", "X2", "T0", "K2/7", "K2/8/100", "K2/8/0/1", "K2/8/0/0/9"]:
+    s = gf2x.parse_spec("T2.K3.K2.K2/8/288/0/1")
+    assert gf2x.spec_text(s) == "T2.K3.K2.K2/8/288/0/1"
+    assert gf2x.spec_text(gf2x.parse_spec("K3")) == "K3/0/0/0/0"
+    for bad in ["K4/8", "X2", "T0", "K2/7", "K2/8/100", "K2/8/0/1", "K2/8/0/0/9", "K3/8/0/0/1", "K2/12/0/0/1",
+                "K2/8/0/0/0/0"]:
         with pytest.raises(gf2x.Gf2xError):
             gf2x.parse_spec(bad)
 

@@ -66,6 +66,8 @@ PLANS_17669 = [
     "T16.K3.K3.K2.K2/8", "K3.K3.K2.K2.K2/10", "K5.K2.K2.K2.K2/8", "K3.K2.K2.K2.K2.K2/6", "K2.K2.K2.K2.K2.K2/10",
     "T2.K3.K2.K2/16", "T2.K3.K2.K2.K2.K2/4", "T2.K5.K2.K2/12", "T2.K3.K2.K2.K2/8/256/0", "T2.K3.K2.K2.K2/8/0/1",
     "K3.K3.K2.K2.K2/10/0/1", "T2.T2.K3.K2/12", "K2.T1.K3.K2.K2/8", "T3.K3.K2.K2.K2/8", "T5.K2.K2.K2.K2.K2/8",
+    "T2.K3.K2.K2.K2/8/0/0/1", "T2.K2.K2.K2.K2.K2/6/0/0/1", "T2.K3.K2.K2.K2.K2/4/0/0/1", "T2.K3.K2.K2.K2/8/0/1/1",
+    "K3.K3.K2.K2.K2/10/0/0/1", "T1.K3.K2.K2.K2/8/128/0/1", "T2.K3.K2.K2/16/0/0/0", "K5.K2.K2.K2.K2/8/0/1/1",
 ]
 
 
@@ -82,7 +84,8 @@ def test_plan_space_hqc128(ctx, spec):
 
 
 PLANS_57637 = ["T16.K5.K2.K2.K2.K2/8/0/1", "K5.K2.K2.K2.K2.K2/12/0/1", "T8.K5.K2.K2.K2/16/0/1",
-               "T2.K3.K3.K2.K2.K2/10/0/1", "T16.K5.K3.K2.K2/12/0/1"]
+               "T2.K3.K3.K2.K2.K2/10/0/1", "T16.K5.K3.K2.K2/12/0/1", "T16.K5.K2.K2.K2.K2/8/0/1/1",
+               "T16.K5.K2.K2.K2.K2/10/0/1/1", "T4.K5.K3.K2.K2.K2/6/0/1/1"]
 
 
 @pytest.mark.parametrize("spec", PLANS_57637)
