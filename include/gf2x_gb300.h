@@ -150,6 +150,13 @@ void gf2x_ctx_destroy(gf2x_ctx *ctx);
  * (spec = NULL restores the default).  Host-side validation only. */
 gf2x_status gf2x_ctx_set_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_plan_spec *spec);
 
+/* Load a plan database written by the autotuner: text lines
+ * "n batch_bucket spec", '#' comments.  For each n the entry whose batch
+ * bucket is nearest (in log2) to batch_hint becomes the context's plan.
+ * GF2X_EINVAL if the file cannot be read or an entry is rejected (the
+ * valid entries are still installed). */
+gf2x_status gf2x_ctx_load_plan_db(gf2x_ctx *ctx, const char *path, size_t batch_hint);
+
 /* The spec the context currently uses for size n. */
 gf2x_status gf2x_ctx_get_plan(gf2x_ctx *ctx, uint32_t n, gf2x_plan_spec *spec);
 

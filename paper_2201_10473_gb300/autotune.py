@@ -1,0 +1,278 @@
+"""Measured plan search for the fused multiplication kernel.
+
+The autotuner enumerates recursion plans for a size n (optional Toom-3 top
+level with several word shifts, non-increasing Karatsuba split sequences,
+every compiled leaf size, fused or shared-memory last level, breadth-first or
+sequential top, several CTA sizes), measures each on the GPU with CUDA events
+in the launch form it will be used in (one persistent batched launch), and
+keeps the fastest.  Every measurement is appended to a JSONL timing log,
+which also trains the learned cost model (costmodel.py).
+
+Plans differ only in how the product is computed, never in its value: before
+a candidate is timed, its outputs on a probe batch are compared with those of
+the context's current plan, and a mismatch is an error.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+import time
+from dataclasses import dataclass
+
+from . import gf2x
+
+TOOM_SHIFTS = (0, 1, 2, 4, 8, 16)
+THREAD_CHOICES = (0, 128, 192, 256, 320, 384, 448, 512, 640, 768)
+
+
+def _kseqs(max_depth: int = 7):
+    out = [()]
+    def rec(cur, maxk, depth):
+        if depth == 0:
+            return
+        for k in (5, 3, 2):
+            if k <= maxk:
+                nxt = cur + (k,)
+                out.append(nxt)
+                rec(nxt, k, depth - 1)
+    rec((), 5, max_depth)
+    return out
+
+
+def candidate_specs(n: int, max_waste: float = 1.30, threads=THREAD_CHOICES, limit: int | None = None):
+    """Valid plan specs for size n whose padded size is at most max_waste * n."""
+    seen = set()
+    out = []
+    for W in TOOM_SHIFTS:
+        for ks in _kseqs():
+            levels = ([f"T{W}"] if W else []) + [f"K{k}" for k in ks]
+            if not levels:
+                continue
+            base = ".".join(levels)
+            for S in (4, 6, 8, 10, 12, 16):
+                for seq in (0, 1):
+                    for fuse in (0, 1):
+                        spec0 = f"{base}/{S}/0/{seq}/{fuse}"
+                        try:
+                            info = gf2x.plan_info(n, spec0)
+                        except gf2x.Gf2xError:
+                            continue
+                        if 32 * info["top_words"] > max_waste * n:
+                            continue
+                        maxT = 768 if S <= 6 else 512
+                        for t in threads:
+                            if t and (t > maxT or t < 64):
+                                continue
+                            spec = f"{base}/{S}/{t}/{seq}/{fuse}"
+                            if t:
+                                try:
+                                    gf2x.plan_info(n, spec)
+                                except gf2x.Gf2xError:
+                                    continue
+                            key = (base, S, t or info["threads"], seq, fuse)
+                            if key in seen:
+                                continue
+                            seen.add(key)
+                            out.append(spec)
+                            if limit and len(out) >= limit:
+                                return out
+    return out
+
+
+@dataclass
+class Measurement:
+    n: int
+    batch: int
+    spec: str
+    ms: float
+    mults_per_s: float
+    threads: int
+    smem_bytes: int
+    blocks_per_sm: int
+
+
+class Autotuner:
+    """Times plan specs for one context; appends every timing to `log_path`."""
+
+    def __init__(self, ctx: gf2x.Context, log_path: str | None = None, reps: int = 5, warmup: int = 2):
+        import torch
+        self.torch = torch
+        self.ctx = ctx
+        self.log_path = log_path
+        self.reps = reps
+        self.warmup = warmup
+        self._inputs = {}
+
+    def _operands(self, n: int, batch: int):
+        key = (n, batch)
+        if key not in self._inputs:
+            torch = self.torch
+            g = torch.Generator(device="cuda")
+            g.manual_seed(n * 1000003 + batch)
+            L = gf2x.limbs(n)
+            a = torch.randint(-2**62, 2**62, (batch, L), dtype=torch.int64, device="cuda", generator=g)
+            b = torch.randint(-2**62, 2**62, (batch, L), dtype=torch.int64, device="cuda", generator=g)
+            out = torch.empty((batch, L), dtype=torch.int64, device="cuda")
+            ref = torch.empty((min(batch, 64), L), dtype=torch.int64, device="cuda")
+            chk = torch.empty_like(ref)
+            self._inputs[key] = (a, b, out, ref, chk)
+        return self._inputs[key]
+
+    def measure(self, n: int, spec: str, batch: int, persistent: bool = True, verify: bool = True) -> Measurement:
+        torch = self.torch
+        a, b, out, ref, chk = self._operands(n, batch)
+        m = ref.shape[0]
+        prev = self.ctx.get_plan(n)
+        if verify:
+            self.ctx.mul_strided(a[:m], b[:m], n, True, out=ref)
+        self.ctx.set_plan(n, spec)
+        try:
+            if verify:
+                self.ctx.mul_strided(a[:m], b[:m], n, True, out=chk)
+                if not torch.equal(ref, chk):
+                    raise RuntimeError(f"plan {spec} disagrees with plan {prev} at n={n}")
+            for _ in range(self.warmup):
+                self.ctx.mul_strided(a, b, n, True, out=out, persistent=persistent)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(self.reps):
+                self.ctx.mul_strided(a, b, n, True, out=out, persistent=persistent)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / self.reps
+            shape = self.ctx.launch_shape(n)
+        finally:
+            self.ctx.set_plan(n, prev)
+        meas = Measurement(n, batch, spec, ms, batch / (ms * 1e-3), shape["threads"], shape["smem_bytes"],
+                           shape["blocks_per_sm"])
+        self._log(meas)
+        return meas
+
+    def _log(self, m: Measurement):
+        if not self.log_path:
+            return
+        info = gf2x.plan_info(m.n, m.spec)
+        rec = dict(m.__dict__)
+        rec.update(ts=time.time(), ops_full=info["ops_full"], top_words=info["top_words"],
+                   nleaves=info["nleaves"])
+        os.makedirs(os.path.dirname(os.path.abspath(self.log_path)), exist_ok=True)
+        with open(self.log_path, "a") as f:
+            f.write(json.dumps(rec) + "\n")
+
+    def search(self, n: int, batch: int, specs=None, budget_s: float | None = None) -> list:
+        """Measure every candidate (or `specs`); returns measurements sorted fastest first."""
+        specs = specs if specs is not None else candidate_specs(n)
+        res = []
+        t0 = time.time()
+        for s in specs:
+            if budget_s is not None and time.time() - t0 > budget_s:
+                break
+            try:
+                res.append(self.measure(n, s, batch))
+            except gf2x.Gf2xError:
+                continue
+        res.sort(key=lambda m: m.ms)
+        return res
+
+
+# ------------------------------------------------------------------ plan database
+# Text file read by the C library (gf2x_ctx_load_plan_db): one line
+# "n batch_bucket spec ms mults_per_s" per tuned (size, batch bucket).
+
+def batch_bucket(batch: int) -> int:
+    """Power-of-two bucket of a batch size (plans are stored per bucket)."""
+    return 1 << max(0, int(math.ceil(math.log2(max(1, batch)))))
+
+
+def load_db(path: str) -> dict:
+    """{(n, bucket): {"spec", "ms", "mults_per_s"}}"""
+    db = {}
+    try:
+        with open(path) as f:
+            for line in f:
+                line = line.split("#", 1)[0].split()
+                if len(line) >= 3:
+                    rec = {"spec": line[2]}
+                    if len(line) >= 5:
+                        rec.update(ms=float(line[3]), mults_per_s=float(line[4]))
+                    db[(int(line[0]), int(line[1]))] = rec
+    except OSError:
+        pass
+    return db
+
+
+def save_db(path: str, db: dict, header: str = ""):
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        f.write("# gf2x_gb300 plan database: n batch_bucket spec ms_per_launch mults_per_s\n")
+        if header:
+            f.write(f"# {header}\n")
+        for (n, bucket), rec in sorted(db.items()):
+            f.write(f"{n} {bucket} {rec['spec']} {rec.get('ms', 0):.4f} {rec.get('mults_per_s', 0):.1f}\n")
+    os.replace(tmp, path)
+
+
+def record_best(db: dict, n: int, batch: int, m: Measurement):
+    db[(n, batch_bucket(batch))] = {"spec": m.spec, "ms": m.ms, "mults_per_s": m.mults_per_s}
+
+
+def read_log(path: str) -> list:
+    out = []
+    try:
+        with open(path) as f:
+            for line in f:
+                line = line.strip()
+                if line:
+                    out.append(json.loads(line))
+    except OSError:
+        pass
+    return out
+
+
+def main(argv=None):
+    """python -m paper_2201_10473_gb300.autotune --sizes 17669,35851 --batches 2048 --log L --db D"""
+    import argparse
+    import random
+
+    p = argparse.ArgumentParser(description=__doc__)
+    p.add_argument("--sizes", default="12323,17669,24659,35851,40973,57637")
+    p.add_argument("--batches", default="2048", help="first batch: exhaustive search; others: --sample candidates")
+    p.add_argument("--sample", type=int, default=200, help="candidates re-measured at the other batch sizes")
+    p.add_argument("--log", required=True)
+    p.add_argument("--db", required=True)
+    p.add_argument("--budget", type=float, default=None, help="seconds per (size, batch) search")
+    p.add_argument("--limit", type=int, default=None)
+    p.add_argument("--seed", type=int, default=1)
+    a = p.parse_args(argv)
+    ctx = gf2x.Context()
+    tuner = Autotuner(ctx, a.log)
+    db = load_db(a.db)
+    rng = random.Random(a.seed)
+    sizes = [int(x) for x in a.sizes.split(",") if x]
+    batches = [int(x) for x in a.batches.split(",") if x]
+    for n in sizes:
+        cands = candidate_specs(n, limit=a.limit)
+        t0 = time.time()
+        res = tuner.search(n, batches[0], cands, a.budget)
+        record_best(db, n, batches[0], res[0])
+        print(f"n={n} batch={batches[0]} measured={len(res)} best={res[0].spec} {res[0].mults_per_s:.4g}/s "
+              f"default={gf2x.default_spec(n)} ({time.time() - t0:.0f}s)", flush=True)
+        for bsz in batches[1:]:
+            sub = [m.spec for m in res[:20]] + rng.sample(cands, min(a.sample, len(cands)))
+            r2 = tuner.search(n, bsz, list(dict.fromkeys(sub)), a.budget)
+            record_best(db, n, bsz, r2[0])
+            print(f"n={n} batch={bsz} measured={len(r2)} best={r2[0].spec} {r2[0].mults_per_s:.4g}/s", flush=True)
+        save_db(a.db, db, header="tuned on " + torch_device_name())
+
+
+def torch_device_name() -> str:
+    import torch
+    return torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+
+
+if __name__ == "__main__":
+    main()

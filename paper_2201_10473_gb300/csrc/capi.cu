@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -56,7 +57,16 @@ struct gf2x_ctx {
     std::string last_error;
     std::vector<DevItem> scratch_items;
     std::vector<uint32_t> scratch_S;
+    std::unordered_map<std::string, uint32_t> slot_of;  // (n, spec, checked) -> plan slot, for reuse
 };
+
+static std::string plan_key(uint32_t n, const gf2x_plan_spec &spec, int checked)
+{
+    std::string k(reinterpret_cast<const char *>(&spec), sizeof(spec));
+    k.append(reinterpret_cast<const char *>(&n), sizeof(n));
+    k.push_back(checked ? 'c' : 'u');
+    return k;
+}
 
 static gf2x_status fail(gf2x_ctx *ctx, gf2x_status st, const std::string &msg)
 {
@@ -174,6 +184,12 @@ extern "C" void gf2x_ctx_destroy(gf2x_ctx *ctx)
 static gf2x_status install_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_plan_spec &spec, int checked,
                                 cudaStream_t stream, uint32_t *slot)
 {
+    const std::string key = plan_key(n, spec, checked);
+    auto found = ctx->slot_of.find(key);
+    if (found != ctx->slot_of.end()) {  // slots never change once written: reuse
+        *slot = found->second;
+        return GF2X_OK;
+    }
     if (ctx->nplans >= kPlanCapacity)
         return fail(ctx, GF2X_EUNSUPPORTED, "plan table full");
     GPlan P;
@@ -187,6 +203,7 @@ static gf2x_status install_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_plan_spec 
                                     stream);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "plan upload");
+    ctx->slot_of[key] = s;
     *slot = s;
     return GF2X_OK;
 }
@@ -628,5 +645,51 @@ extern "C" gf2x_status gf2x_ctx_launch_shape(gf2x_ctx *ctx, uint32_t n, uint32_t
         *blocks_per_sm = (uint32_t)per_sm;
     if (sm_count)
         *sm_count = (uint32_t)ctx->sm_count;
+    return GF2X_OK;
+}
+
+// Plan database: text lines "n batch_bucket spec [anything]"; '#' starts a comment.
+// For every n the entry whose bucket is nearest (in log2) to batch_hint wins.
+extern "C" gf2x_status gf2x_ctx_load_plan_db(gf2x_ctx *ctx, const char *path, size_t batch_hint)
+{
+    if (!ctx || !path)
+        return GF2X_EINVAL;
+    FILE *f = fopen(path, "r");
+    if (!f)
+        return fail(ctx, GF2X_EINVAL, std::string("cannot open plan database ") + path);
+    struct Best {
+        double dist;
+        gf2x_plan_spec spec;
+    };
+    std::unordered_map<uint32_t, Best> best;
+    char line[512];
+    const double want = std::log2((double)std::max<size_t>(1, batch_hint));
+    gf2x_status st = GF2X_OK;
+    while (fgets(line, sizeof(line), f)) {
+        char *hash = strchr(line, '#');
+        if (hash)
+            *hash = '\0';
+        unsigned long n = 0, bucket = 0;
+        char spec_text[256];
+        if (sscanf(line, "%lu %lu %255s", &n, &bucket, spec_text) != 3)
+            continue;
+        gf2x_plan_spec spec;
+        if (parse_spec(spec_text, &spec) != GF2X_OK || n < 1 || n > GF2X_MAX_N || bucket < 1) {
+            st = GF2X_EINVAL;
+            continue;
+        }
+        const double d = std::fabs(std::log2((double)bucket) - want);
+        auto it = best.find((uint32_t)n);
+        if (it == best.end() || d < it->second.dist)
+            best[(uint32_t)n] = Best{d, spec};
+    }
+    fclose(f);
+    for (auto &kv : best) {
+        gf2x_status s2 = gf2x_ctx_set_plan(ctx, kv.first, &kv.second.spec);
+        if (s2 != GF2X_OK)
+            st = s2;
+    }
+    if (st != GF2X_OK)
+        return fail(ctx, st, "some plan database entries were rejected");
     return GF2X_OK;
 }

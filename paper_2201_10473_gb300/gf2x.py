@@ -81,6 +81,7 @@ _SIGNATURES = {
                                ctypes.POINTER(_U32)], _I),
     "gf2x_ctx_sync_status": ([_P, _P], _I),
     "gf2x_ctx_last_error": ([_P], ctypes.c_char_p),
+    "gf2x_ctx_load_plan_db": ([_P, ctypes.c_char_p, _SZ], _I),
 }
 
 
@@ -201,6 +202,10 @@ class Context:
         s = PlanSpec()
         self._raise(lib().gf2x_ctx_get_plan(self._h, n, ctypes.byref(s)), "get_plan")
         return spec_text(s)
+
+    def load_plan_db(self, path: str, batch_hint: int = 4096):
+        """Install the tuned plans of a plan database file (see autotune.py)."""
+        self._raise(lib().gf2x_ctx_load_plan_db(self._h, path.encode(), batch_hint), "load_plan_db")
 
     def set_checked(self, on: bool):
         self._raise(lib().gf2x_ctx_set_checked(self._h, 1 if on else 0), "set_checked")
