@@ -192,7 +192,9 @@ gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, co
  *    by the kernel, which looks each plan up by n on the device; every n
  *    must have been prepared (gf2x_ctx_prepare) and all prepared plans must
  *    share one leaf size (else GF2X_EUNSUPPORTED).  An item whose n has no
- *    plan is skipped and reported by gf2x_ctx_sync_status.  Nothing is
+ *    plan is skipped and reported by gf2x_ctx_sync_status; an item with
+ *    n = 0 is an empty slot, skipped silently (padding for fixed-size
+ *    captured launches).  Nothing is
  *    checked on the host and nothing is copied, so the call can be captured
  *    in a CUDA graph; the array must stay valid until the work completes.
  *  - GF2X_BATCH_PERSISTENT: a grid of (SMs x resident CTAs), each CTA
@@ -218,6 +220,33 @@ gf2x_status gf2x_ctx_sync_status(gf2x_ctx *ctx, gf2x_stream stream);
 /* Text of the last error recorded in the context (static until the next
  * call on it). */
 const char *gf2x_ctx_last_error(gf2x_ctx *ctx);
+
+/* ---- Plan cost model network (the autotuner's learned part) -------------
+ * A two-layer perceptron y = w2 . relu(W1 x + b1) + b2 in fp32 that predicts
+ * the log time of a recursion plan from its descriptor.  The paper has no
+ * counterpart: it chooses constructions per degree by measurement (Sec. 3,
+ * Tables tab:perfToom3KR, tab:perfCompToom3K3); the network only orders the
+ * candidates the autotuner measures.  All pointers are device pointers; the
+ * parameter vector is W1 [hidden x in_dim] row-major, b1 [hidden],
+ * w2 [hidden], b2 [1] (gf2x_mlp_param_count floats).  1 <= in_dim <= 64,
+ * 1 <= hidden <= 128, else GF2X_EINVAL.  Asynchronous on `stream`. */
+
+/* Number of fp32 parameters of the network. */
+size_t gf2x_mlp_param_count(int in_dim, int hidden);
+
+/* y[s] = network(x[s]) for s < batch; x is [batch x in_dim] row-major. */
+gf2x_status gf2x_mlp_forward(const float *params, const float *x, float *y, int batch, int in_dim, int hidden,
+                             gf2x_stream stream);
+
+/* Gradient of L = (1/batch) sum_s (y_s - target_s)^2 with respect to the
+ * parameters into grad (overwritten), and L into *loss (device float). */
+gf2x_status gf2x_mlp_grad(const float *params, const float *x, const float *target, float *grad, float *loss,
+                          int batch, int in_dim, int hidden, gf2x_stream stream);
+
+/* One Adam step (Kingma & Ba, with bias correction for step >= 1) on
+ * params using grad and the moment buffers m, v (nparams floats each). */
+gf2x_status gf2x_mlp_adam(float *params, const float *grad, float *m, float *v, size_t nparams, float lr,
+                          float beta1, float beta2, float eps, int step, gf2x_stream stream);
 
 #ifdef __cplusplus
 }

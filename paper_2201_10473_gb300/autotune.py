@@ -248,16 +248,20 @@ def main(argv=None):
     p.add_argument("--limit", type=int, default=None)
     p.add_argument("--seed", type=int, default=1)
     a = p.parse_args(argv)
-    ctx = gf2x.Context()
-    tuner = Autotuner(ctx, a.log)
     db = load_db(a.db)
     rng = random.Random(a.seed)
     sizes = [int(x) for x in a.sizes.split(",") if x]
     batches = [int(x) for x in a.batches.split(",") if x]
     for n in sizes:
+        ctx = gf2x.Context()          # a fresh plan table per size
+        tuner = Autotuner(ctx, a.log)
         cands = candidate_specs(n, limit=a.limit)
         t0 = time.time()
         res = tuner.search(n, batches[0], cands, a.budget)
+        if not res:
+            print(f"n={n}: no candidate could be measured", flush=True)
+            ctx.close()
+            continue
         record_best(db, n, batches[0], res[0])
         print(f"n={n} batch={batches[0]} measured={len(res)} best={res[0].spec} {res[0].mults_per_s:.4g}/s "
               f"default={gf2x.default_spec(n)} ({time.time() - t0:.0f}s)", flush=True)
@@ -267,6 +271,7 @@ def main(argv=None):
             record_best(db, n, bsz, r2[0])
             print(f"n={n} batch={bsz} measured={len(r2)} best={r2[0].spec} {r2[0].mults_per_s:.4g}/s", flush=True)
         save_db(a.db, db, header="tuned on " + torch_device_name())
+        ctx.close()
 
 
 def torch_device_name() -> str:

@@ -1,0 +1,231 @@
+"""Learned plan cost model: a 2-layer MLP (64 hidden units, ReLU, fp32) that
+predicts log2(ns per product) of a recursion plan from its descriptor.
+
+It is trained on the autotuner's own timing log by the library's CUDA kernels
+(gf2x_mlp_grad / gf2x_mlp_adam, forward by gf2x_mlp_forward); torch only
+holds the device buffers.  Given a size and a batch it orders the candidate
+plans so that only the first few are measured; exhaustive measured search
+remains the fallback and the judge of its regret (evaluate_gain).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import gf2x
+
+IN_DIM = 16
+HIDDEN = 64
+
+_MLP_SIGS = {
+    "gf2x_mlp_param_count": ([ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
+    "gf2x_mlp_forward": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "gf2x_mlp_grad": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "gf2x_mlp_adam": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                       ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int,
+                       ctypes.c_void_p], ctypes.c_int),
+}
+
+
+def _lib():
+    L = gf2x.lib()
+    if not getattr(L, "_mlp_sigs", False):
+        for name, (args, res) in _MLP_SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        L._mlp_sigs = True
+    return L
+
+
+def _check(st, where):
+    if st:
+        raise gf2x.Gf2xError(st, where)
+
+
+def param_count(in_dim: int = IN_DIM, hidden: int = HIDDEN) -> int:
+    return int(_lib().gf2x_mlp_param_count(in_dim, hidden))
+
+
+# ------------------------------------------------------------------ features
+
+_info_cache: dict = {}
+
+
+def plan_features(n: int, batch: int, spec: str) -> np.ndarray:
+    """Descriptor of (n, batch, plan) as IN_DIM floats; host only."""
+    key = (n, spec)
+    if key not in _info_cache:
+        _info_cache[key] = gf2x.plan_info(n, spec)
+    info = _info_cache[key]
+    s = gf2x.parse_spec(spec)
+    kinds = [(s.kind[i], s.arg[i]) for i in range(s.nlev)]
+    toomW = [a for k, a in kinds if k == gf2x.LEVEL_TOOM3]
+    ks = [a for k, a in kinds if k == gf2x.LEVEL_KARATSUBA]
+    f = np.zeros(IN_DIM, dtype=np.float32)
+    f[0] = math.log2(n) / 16
+    f[1] = math.log2(max(1, batch)) / 13
+    f[2] = 32 * info["top_words"] / n - 1
+    f[3] = s.nlev / 8
+    f[4] = len(toomW)
+    f[5] = (math.log2(toomW[0] + 1) / 5) if toomW else 0.0
+    f[6] = ks.count(2) / 7
+    f[7] = ks.count(3) / 3
+    f[8] = ks.count(5) / 2
+    f[9] = info["leaf_words"] / 16
+    f[10] = s.fuse_leaf
+    f[11] = s.seq_top
+    f[12] = info["threads"] / 768
+    f[13] = math.log2(info["ops_full"]) / 30
+    f[14] = math.log2(max(1, info["nleaves"])) / 14
+    f[15] = info["smem_bytes"] / 232448
+    return f
+
+
+def target_of(rec: dict) -> float:
+    """log2 of nanoseconds per product of one timing-log record."""
+    return math.log2(rec["ms"] * 1e6 / rec["batch"])
+
+
+# ------------------------------------------------------------------ network
+
+class CostModel:
+    def __init__(self, hidden: int = HIDDEN, seed: int = 0):
+        import torch
+        self.torch = torch
+        self.hidden = hidden
+        self.np = param_count(IN_DIM, hidden)
+        rng = np.random.default_rng(seed)
+        p = np.zeros(self.np, dtype=np.float32)
+        D, H = IN_DIM, hidden
+        p[: H * D] = rng.normal(0, math.sqrt(2.0 / D), size=H * D)      # He initialisation
+        p[H * D + H: H * D + 2 * H] = rng.normal(0, math.sqrt(1.0 / H), size=H)
+        self.params = torch.from_numpy(p).cuda()
+        self.mu = np.zeros(IN_DIM, dtype=np.float32)
+        self.sd = np.ones(IN_DIM, dtype=np.float32)
+        self.t_mu = 0.0
+        self.t_sd = 1.0
+
+    # normalisation of inputs and targets from the training set
+    def _norm(self, X: np.ndarray) -> np.ndarray:
+        return ((X - self.mu) / self.sd).astype(np.float32)
+
+    def fit(self, records: list, steps: int = 3000, lr: float = 3e-3, batch: int = 2048, seed: int = 0) -> list:
+        torch = self.torch
+        X = np.stack([plan_features(r["n"], r["batch"], r["spec"]) for r in records])
+        T = np.array([target_of(r) for r in records], dtype=np.float32)
+        self.mu = X.mean(axis=0)
+        self.sd = X.std(axis=0) + 1e-3
+        self.t_mu = float(T.mean())
+        self.t_sd = float(T.std() + 1e-6)
+        Xd = torch.from_numpy(self._norm(X)).cuda()
+        Td = torch.from_numpy(((T - self.t_mu) / self.t_sd).astype(np.float32)).cuda()
+        G = torch.zeros(self.np, dtype=torch.float32, device="cuda")
+        M = torch.zeros_like(G)
+        V = torch.zeros_like(G)
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        L = _lib()
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(seed)
+        N = X.shape[0]
+        hist = []
+        for step in range(1, steps + 1):
+            if batch >= N:
+                xb, tb = Xd, Td
+            else:
+                idx = torch.randint(0, N, (batch,), device="cuda", generator=gen)
+                xb, tb = Xd[idx].contiguous(), Td[idx].contiguous()
+            _check(L.gf2x_mlp_grad(self.params.data_ptr(), xb.data_ptr(), tb.data_ptr(), G.data_ptr(),
+                                   loss.data_ptr(), xb.shape[0], IN_DIM, self.hidden, stream), "gf2x_mlp_grad")
+            _check(L.gf2x_mlp_adam(self.params.data_ptr(), G.data_ptr(), M.data_ptr(), V.data_ptr(), self.np, lr,
+                                   0.9, 0.999, 1e-8, step, stream), "gf2x_mlp_adam")
+            if step % 100 == 0 or step == steps:
+                hist.append(float(loss.item()))
+        return hist
+
+    def predict_features(self, X: np.ndarray) -> np.ndarray:
+        torch = self.torch
+        Xd = torch.from_numpy(self._norm(np.asarray(X, dtype=np.float32))).cuda()
+        Y = torch.empty(Xd.shape[0], dtype=torch.float32, device="cuda")
+        _check(_lib().gf2x_mlp_forward(self.params.data_ptr(), Xd.data_ptr(), Y.data_ptr(), Xd.shape[0], IN_DIM,
+                                       self.hidden, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+               "gf2x_mlp_forward")
+        return Y.cpu().numpy().astype(np.float64) * self.t_sd + self.t_mu
+
+    def predict(self, n: int, batch: int, specs) -> np.ndarray:
+        """Predicted log2(ns per product) of every spec."""
+        if not specs:
+            return np.zeros(0)
+        return self.predict_features(np.stack([plan_features(n, batch, s) for s in specs]))
+
+    def rank(self, n: int, batch: int, specs) -> list:
+        pred = self.predict(n, batch, specs)
+        return [specs[i] for i in np.argsort(pred, kind="stable")]
+
+    # checkpoint
+    def state(self) -> dict:
+        return {"params": self.params.cpu().numpy(), "mu": self.mu, "sd": self.sd,
+                "t": np.array([self.t_mu, self.t_sd]), "hidden": np.array([self.hidden])}
+
+    def save(self, path: str):
+        np.savez(path, **self.state())
+
+    @classmethod
+    def load(cls, path: str) -> "CostModel":
+        d = np.load(path)
+        m = cls(hidden=int(d["hidden"][0]))
+        m.params.copy_(m.torch.from_numpy(d["params"].astype(np.float32)))
+        m.mu, m.sd = d["mu"], d["sd"]
+        m.t_mu, m.t_sd = float(d["t"][0]), float(d["t"][1])
+        return m
+
+
+# ------------------------------------------------------------------ gain over the method without it
+
+def measurements_to_within(order: list, times: dict, tol: float = 0.05) -> int:
+    """1-based position in `order` of the first plan within (1+tol) of the best time."""
+    best = min(times.values())
+    for i, s in enumerate(order):
+        if times[s] <= best * (1 + tol):
+            return i + 1
+    return len(order)
+
+
+def random_order_expectation(times: dict, tol: float = 0.05) -> float:
+    """Expected position of the first good plan when candidates are measured in random order."""
+    best = min(times.values())
+    g = sum(1 for t in times.values() if t <= best * (1 + tol))
+    return (len(times) + 1) / (g + 1)
+
+
+def evaluate_gain(records: list, holdout_n: int, batch: int, k: int = 10, steps: int = 3000, seed: int = 0) -> dict:
+    """Train on every size but `holdout_n`, then rank holdout_n's measured candidates.
+
+    Returns the measurements needed to come within 5% of the exhaustive best
+    (model order vs. the expectation of random order), and the regret of
+    measuring only the model's top k."""
+    train = [r for r in records if r["n"] != holdout_n]
+    test = {}
+    for r in records:
+        if r["n"] == holdout_n and r["batch"] == batch:
+            test[r["spec"]] = min(test.get(r["spec"], float("inf")), r["ms"])
+    if not test or not train:
+        raise ValueError("no data for this split")
+    model = CostModel(seed=seed)
+    hist = model.fit(train, steps=steps, seed=seed)
+    specs = sorted(test)
+    order = model.rank(holdout_n, batch, specs)
+    best = min(test.values())
+    topk_best = min(test[s] for s in order[:k])
+    default = gf2x.default_spec(holdout_n)
+    return {"n": holdout_n, "batch": batch, "candidates": len(specs),
+            "model_measurements_to_5pct": measurements_to_within(order, test),
+            "random_expected_measurements_to_5pct": random_order_expectation(test),
+            "regret_top_k": topk_best / best - 1.0, "k": k,
+            "default_plan_regret": (test[default] / best - 1.0) if default in test else None,
+            "final_train_loss": hist[-1] if hist else None}

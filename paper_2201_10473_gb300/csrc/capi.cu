@@ -22,7 +22,7 @@ using namespace gf2x;
 
 namespace {
 
-constexpr uint32_t kPlanCapacity = 4096;  // distinct (n, spec) plans per context
+constexpr uint32_t kPlanCapacity = 8192;  // distinct (n, spec) plans per context
 constexpr int kRing = 4;                  // item staging buffers
 
 struct PlanEntry {
@@ -58,6 +58,7 @@ struct gf2x_ctx {
     std::vector<DevItem> scratch_items;
     std::vector<uint32_t> scratch_S;
     std::unordered_map<std::string, uint32_t> slot_of;  // (n, spec, checked) -> plan slot, for reuse
+    std::unordered_map<uint64_t, int> occupancy;        // (leaf, threads, smem) -> resident CTAs per SM
 };
 
 static std::string plan_key(uint32_t n, const gf2x_plan_spec &spec, int checked)
@@ -338,10 +339,18 @@ static gf2x_status launch(gf2x_ctx *ctx, const LaunchArgs &args, uint32_t S, uns
     unsigned grid;
     LaunchArgs a = args;
     if (persistent) {
+        // cached so that launches inside a CUDA graph capture make no occupancy query
+        const uint64_t okey = ((uint64_t)S << 48) | ((uint64_t)threads << 32) | (uint64_t)smem;
         int per_sm = 0;
-        cudaError_t e = preparer_for(S)(&per_sm, threads, smem);
-        if (e != cudaSuccess)
-            return cuda_fail(ctx, e, "occupancy query");
+        auto oc = ctx->occupancy.find(okey);
+        if (oc != ctx->occupancy.end()) {
+            per_sm = oc->second;
+        } else {
+            cudaError_t e = preparer_for(S)(&per_sm, threads, smem);
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e, "occupancy query");
+            ctx->occupancy[okey] = per_sm;
+        }
         if (per_sm < 1)
             return fail(ctx, GF2X_EUNSUPPORTED, "kernel does not fit on an SM");
         grid = (unsigned)std::min<size_t>(count, (size_t)per_sm * ctx->sm_count);

@@ -589,7 +589,7 @@ __device__ __forceinline__ DevItem fetch_item(const LaunchArgs &args, uint32_t i
         return args.items[i];
     if (args.mode == kItemsUser) {
         DevItem it = args.items[i];
-        it.plan = it.plan <= 131072u ? __ldg(args.plan_of_n + it.plan) : kNoPlan;
+        it.plan = it.plan == 0u ? kEmptyItem : (it.plan <= 131072u ? __ldg(args.plan_of_n + it.plan) : kNoPlan);
         return it;
     }
     DevItem it = args.base;
@@ -615,8 +615,8 @@ fused_mul_kernel(const LaunchArgs args)
     const uint32_t step = args.persistent ? gridDim.x : args.count;
     for (uint32_t i = blockIdx.x; i < args.count; i += step) {
         const DevItem it = fetch_item(args, i);
-        if (it.plan == kNoPlan) {  // uniform over the CTA: every thread read the same item
-            if (threadIdx.x == 0)
+        if (it.plan >= kEmptyItem) {  // uniform over the CTA: every thread read the same item
+            if (it.plan == kNoPlan && threadIdx.x == 0)
                 flag_error(args.err, kErrNoPlan);
             continue;
         }

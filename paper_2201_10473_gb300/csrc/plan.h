@@ -98,6 +98,7 @@ struct LaunchArgs {
 // fourth field is n instead of a plan slot.
 enum : uint32_t { kItemsSingle = 0, kItemsArray = 1, kItemsStrided = 2, kItemsUser = 3 };
 constexpr uint32_t kNoPlan = 0xffffffffu;
+constexpr uint32_t kEmptyItem = 0xfffffffeu;  // device item with n = 0: a padding slot, skipped
 
 // Checked-mode error codes (bit flags, OR-ed into *err).
 enum : uint32_t { kErrDivX = 1, kErrDivX1 = 2, kErrPad = 4, kErrNoPlan = 8 };

@@ -230,3 +230,77 @@ def test_sparse_weight_131_through_dense_path(ctx, n):
     b = wl.sparse_operands(4400, n, 131, 4)
     assert all(int(np.unpackbits(row.view(np.uint8)).sum()) == 131 for row in b)
     check_batch(ctx, a, b, n, True)
+
+
+def _device_item_ctx():
+    from paper_2201_10473_gb300 import Context
+    c2 = Context(0)
+    plans = {17669: "T2.K3.K2.K2.K2/8", 35851: "T2.K3.K2.K2.K2.K2/8/0/1", 57637: "T16.K5.K2.K2.K2.K2/8/0/1"}
+    for n, s in plans.items():
+        c2.set_plan(n, s)
+    c2.prepare(list(plans))
+    return c2
+
+
+def test_device_items_padding_and_cuda_graph_replay():
+    """Empty (n = 0) slots are skipped; a captured persistent launch replays
+    correctly, also after the operands change in place."""
+    from paper_2201_10473_gb300 import pack_items
+    c2 = _device_item_ctx()
+    try:
+        sizes = wl.shuffle(79, [17669] * 3 + [35851] * 2 + [57637] * 2)
+        ops = wl.mixed_operands(5200, sizes)
+        dev, rows, outs = [], [], []
+        for (a, b), n in zip(ops, sizes):
+            da, db = to_dev(a), to_dev(b)
+            o = torch.zeros(wl.limbs(n), dtype=torch.int64, device="cuda")
+            dev.append((da, db))
+            outs.append(o)
+            rows.append((da.data_ptr(), db.data_ptr(), o.data_ptr(), n, 1))
+            rows.append((0, 0, 0, 0, 0))                      # padding slot
+        items = pack_items(rows).cuda()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            c2.mul_batched_device(items, len(rows), persistent=True)   # warm-up outside capture
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            c2.mul_batched_device(items, len(rows), persistent=True)
+        for o in outs:
+            o.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        c2.sync_status()
+        for (a, b), n, o in zip(ops, sizes, outs):
+            assert np.array_equal(to_host(o), oracle.mulmod(a, b, n)), n
+        # new operand values, same buffers: replay computes the new products
+        ops2 = wl.mixed_operands(5300, sizes)
+        for (a, b), (da, db) in zip(ops2, dev):
+            da.copy_(to_dev(a))
+            db.copy_(to_dev(b))
+        g.replay()
+        torch.cuda.synchronize()
+        for (a, b), n, o in zip(ops2, sizes, outs):
+            assert np.array_equal(to_host(o), oracle.mulmod(a, b, n)), n
+    finally:
+        c2.close()
+
+
+def test_device_item_without_plan_is_reported():
+    from paper_2201_10473_gb300 import Gf2xError, pack_items
+    c2 = _device_item_ctx()
+    try:
+        n = 1000   # not prepared
+        a, b = wl.dense_pair(5400, n, 1)
+        da, db = to_dev(a[0]), to_dev(b[0])
+        o = torch.zeros(wl.limbs(n), dtype=torch.int64, device="cuda")
+        items = pack_items([(da.data_ptr(), db.data_ptr(), o.data_ptr(), n, 1)]).cuda()
+        c2.mul_batched_device(items, 1)
+        with pytest.raises(Gf2xError) as e:
+            c2.sync_status()
+        assert e.value.status == 7
+        c2.sync_status()   # the report is cleared
+    finally:
+        c2.close()
