@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="hqc128")
     p.add_argument("--no-plain", action="store_true", help="skip the plain one-launch-per-product measurement")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle cpu_baseline sample")
+    p.add_argument("--no-extras", action="store_true", help="skip the other workloads (C1, C3, C4, C5)")
+    p.add_argument("--serving-requests", type=int, default=200000)
     return p.parse_args()
 
 
@@ -217,7 +219,7 @@ def run_ours(args, w):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n, batch, reduce = w["n"], w["batch"], w["reduce"]
     seed = wl.BASE_SEED + w["key"]
-    ctx = Context(local)
+    ctx = Context(local, batch_hint=batch)
     spec = ctx.get_plan(n)
     info = plan_info(n, spec)
     shape = ctx.launch_shape(n)
@@ -367,6 +369,9 @@ def run_ours(args, w):
     cpu = None
     if world == 1:
         cpu = oracle_rate(w, args.cpu_seconds)
+    extras = None
+    if world == 1 and not args.no_extras:
+        extras = run_extras(args, local)
 
     line = {
         "metric": metric_name(),
@@ -393,10 +398,227 @@ def run_ours(args, w):
         "clocks": clk,
         "parity_checked": import_oracle_ok,
         "e2e_sample_ok": bool(got_e2e.shape[0] == batch),
+        "workloads": extras,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- the other workloads
+
+def _time_calls(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.uint64).view(np.int64)).cuda()
+
+
+def _host(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def run_c1(device):
+    """256 full products at n=12323, one plain launch per product, all checked."""
+    import torch
+
+    import oracle
+    from paper_2201_10473_gb300 import Context
+    n, count = 12323, 256
+    ctx = Context(device, batch_hint=count)
+    a, b = wl.dense_pair(wl.BASE_SEED + 1, n, count)
+    da, db = _dev(a), _dev(b)
+    out = torch.empty((count, (2 * n - 1 + 63) // 64), dtype=torch.int64, device="cuda")
+
+    def plain():
+        for p in range(count):
+            ctx.mul(da[p], db[p], n, out=out[p])
+    ms = _time_calls(plain, 3, 1)
+    ok = bool(np.array_equal(_host(out), oracle.mul_batch(a, b, n, reduce=False)))
+    ms_b = _time_calls(lambda: ctx.mul_strided(da, db, n, False, out=out, persistent=True), 10, 3)
+    ctx.close()
+    return {"workload": "plain-12323-full", "n": n, "products": count, "plan": ctx_plan_text(n, count),
+            "plain_mults_per_s": count / (ms * 1e-3), "batched_mults_per_s": count / (ms_b * 1e-3),
+            "all_checked_against_oracle": ok}
+
+
+def ctx_plan_text(n, batch):
+    from paper_2201_10473_gb300 import Context
+    c = Context(batch_hint=batch)
+    t = c.get_plan(n)
+    c.close()
+    return t
+
+
+def run_c3(device):
+    """2048@17669 + 1024@35851 + 512@57637 interleaved, ONE persistent launch
+    over device items replayed from a CUDA graph, vs plain and per-size launches."""
+    import torch
+
+    import oracle
+    from paper_2201_10473_gb300 import Context, autotune, pack_items, serve
+    wk = wl.workload(3)
+    sizes = np.array(wk.sizes)
+    weights = {n: int((sizes == n).sum()) for n in np.unique(sizes)}
+    reqs = serve.make_requests(sizes, lambda n, c: wl.dense_pair(wk.seed + n, n, c))
+    outs = {n: torch.zeros((cnt, wl.limbs(n)), dtype=torch.int64, device="cuda") for n, cnt in weights.items()}
+    pa, pb = reqs.ptrs(np.arange(len(sizes)))
+    po = np.array([outs[int(n)].data_ptr() + int(i) * 8 * wl.limbs(int(n)) for n, i in zip(sizes, reqs.index)])
+    items = pack_items(list(zip(pa, pb, po, sizes, [1] * len(sizes)))).cuda()
+    log = autotune.packaged_log()
+    best = None
+    for plans in autotune.mixed_plan_sets(log, weights, 2048, top=3):
+        ctx = Context(device, plan_db=None)
+        for n, sp in plans.items():
+            ctx.set_plan(int(n), sp)
+        ctx.prepare(sorted(int(n) for n in weights))
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            ctx.mul_batched_device(items, len(sizes), persistent=True)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            ctx.mul_batched_device(items, len(sizes), persistent=True)
+        ms = _time_calls(g.replay, 10, 3)
+        ctx.sync_status()
+        if best is None or ms < best[0]:
+            best = (ms, plans)
+        ctx.close()
+    ms, plans = best
+    # recompute with the best set and check a sample against the oracle
+    ctx = Context(device, plan_db=None)
+    for n, sp in plans.items():
+        ctx.set_plan(int(n), sp)
+    ctx.prepare(sorted(int(n) for n in weights))
+    for o in outs.values():
+        o.zero_()
+    ctx.mul_batched_device(items, len(sizes), persistent=True)
+    torch.cuda.synchronize()
+    ok = True
+    for r in range(0, len(sizes), 149):
+        n, i = int(sizes[r]), int(reqs.index[r])
+        got = _host(outs[n][i])
+        ok &= bool(np.array_equal(got, oracle.mulmod(_host(reqs.a[n][i]), _host(reqs.b[n][i]), n)))
+    # plain: one launch of one CTA per product
+    def plain():
+        for r in range(len(sizes)):
+            n, i = int(sizes[r]), int(reqs.index[r])
+            ctx.mulmod(reqs.a[n][i], reqs.b[n][i], n, out=outs[n][i])
+    ms_plain = _time_calls(plain, 1, 1)
+    ctx.close()
+    # per-size launches with each size's own tuned plan
+    ctx2 = Context(device, batch_hint=2048)
+
+    def grouped():
+        for n in weights:
+            ctx2.mul_strided(reqs.a[int(n)], reqs.b[int(n)], int(n), True, out=outs[int(n)], persistent=True)
+    ms_grouped = _time_calls(grouped, 10, 3)
+    ctx2.close()
+    total = len(sizes)
+    return {"workload": wk.name, "products": total, "plans": {str(k): v for k, v in plans.items()},
+            "one_launch_graph_mults_per_s": total / (ms * 1e-3),
+            "plain_mults_per_s": total / (ms_plain * 1e-3),
+            "per_size_launches_mults_per_s": total / (ms_grouped * 1e-3),
+            "sample_checked_against_oracle": ok}
+
+
+def run_c4(device):
+    """16384 products at n=57637: dense, and sparse (weight 131) x dense through the same path."""
+    import torch
+
+    import oracle
+    from paper_2201_10473_gb300 import Context
+    n, count = 57637, 16384
+    ctx = Context(device, batch_hint=count)
+    wk = wl.workload(4)
+    a, b = wl.dense_pair(wk.seed, n, count)
+    bs = wl.sparse_operands(wk.seed, n, 131, count)
+    da, db, dbs = _dev(a), _dev(b), _dev(bs)
+    out = torch.empty((count, wl.limbs(n)), dtype=torch.int64, device="cuda")
+    ms_dense = _time_calls(lambda: ctx.mul_strided(da, db, n, True, out=out, persistent=True), 5, 2)
+    sample = np.arange(0, count, 2048)
+    ok = bool(np.array_equal(_host(out)[sample], oracle.mul_batch(a[sample], b[sample], n, reduce=True)))
+    ms_sparse = _time_calls(lambda: ctx.mul_strided(da, dbs, n, True, out=out, persistent=True), 5, 2)
+    ok &= bool(np.array_equal(_host(out)[sample], oracle.mul_batch(a[sample], bs[sample], n, reduce=True)))
+    plan = ctx.get_plan(n)
+    ctx.close()
+    return {"workload": wk.name, "products": count, "plan": plan,
+            "dense_mults_per_s": count / (ms_dense * 1e-3), "sparse131_mults_per_s": count / (ms_sparse * 1e-3),
+            "sparse_over_dense_time": ms_sparse / ms_dense,
+            "note": "sparse operand goes through the dense constant-time path (same work, same time)",
+            "sample_checked_against_oracle": ok}
+
+
+def run_c5(device, requests):
+    """Serving: Poisson arrivals, HBM-budget admission, continuous batching."""
+    import torch  # noqa: F401
+
+    from paper_2201_10473_gb300 import Context, autotune, serve
+    wk = wl.workload(5)
+    sizes = np.array(wk.sizes[:requests])
+    distinct = 4096
+    sub = {}
+
+    def operands(n, c):
+        if n not in sub:
+            sub[n] = wl.dense_pair(wk.seed + n, n, min(c, distinct))
+        a, b = sub[n]
+        reps = -(-c // a.shape[0])
+        return np.tile(a, (reps, 1))[:c], np.tile(b, (reps, 1))[:c]
+    reqs = serve.make_requests(sizes, operands)
+    weights = {int(n): 1 for n in wl.SERVING_SIZES}
+    plans = autotune.mixed_plan_sets(autotune.packaged_log(), weights, 2048, top=1)[0]
+    ctx = Context(device, plan_db=None)
+    for n, sp in plans.items():
+        ctx.set_plan(n, sp)
+    budget = 64 << 20
+    srv = serve.Server(ctx, weights, budget, max_batch=2048, streams=3, use_graphs=True)
+    closed = srv.run(reqs, np.zeros(len(sizes)))
+    cap = closed.completed / closed.wall_s
+    out = {"workload": wk.name, "requests": len(sizes), "budget_bytes": budget, "plans": {str(k): v for k, v in plans.items()},
+           "closed_loop": closed.summary(), "loads": {}}
+    for f in (0.5, 0.8, 0.95, 1.2):
+        arr = wl.poisson_arrivals(wk.seed + int(f * 100), len(sizes), f * cap)
+        r = srv.run(reqs, arr)
+        out["loads"][str(f)] = dict(r.summary(), offered_per_s=f * cap)
+    ctx.sync_status()
+    # plain per-request launches on a subset
+    m = min(4000, len(sizes))
+    sub_reqs = serve.RequestSet(reqs.sizes[:m], reqs.index[:m], reqs.a, reqs.b)
+    pool = serve.SlotPool(weights, budget)
+    pc = serve.serve_plain(ctx, sub_reqs, np.zeros(m), pool, streams=3)
+    pcap = pc.completed / pc.wall_s
+    arr = wl.poisson_arrivals(wk.seed + 7, m, 0.8 * pcap)
+    pl = serve.serve_plain(ctx, sub_reqs, arr, pool, streams=3)
+    out["plain"] = {"requests": m, "closed_loop": pc.summary(), "load_0.8": dict(pl.summary(), offered_per_s=0.8 * pcap)}
+    ctx.close()
+    return out
+
+
+def run_extras(args, device):
+    res = {}
+    for name, fn in (("c1", lambda: run_c1(device)), ("c3", lambda: run_c3(device)), ("c4", lambda: run_c4(device)),
+                     ("c5", lambda: run_c5(device, args.serving_requests))):
+        t0 = time.time()
+        try:
+            res[name] = fn()
+        except Exception as e:  # report, keep the main line
+            res[name] = {"error": f"{type(e).__name__}: {e}"}
+        res[name]["seconds"] = round(time.time() - t0, 1)
+    return res
 
 
 def main():

@@ -178,6 +178,52 @@ class Autotuner:
         return res
 
 
+def guided_search(tuner: "Autotuner", n: int, batch: int, model=None, k: int = 10) -> list:
+    """Measure only the k candidates the cost model ranks fastest; without a
+    model, fall back to exhaustive measured search."""
+    cands = candidate_specs(n)
+    if model is None:
+        return tuner.search(n, batch, cands)
+    return tuner.search(n, batch, model.rank(n, batch, cands)[:k])
+
+
+def mixed_plan_sets(records: list, weights: dict, batch: int, top: int = 3) -> list:
+    """Candidate plan sets for ONE launch over several sizes, from a timing log.
+
+    A mixed launch needs one leaf size (one kernel) and runs every CTA with
+    the largest thread count and shared memory of its plans, so the sets are
+    formed per (leaf size, CTA threads): for each size the fastest measured
+    plan with that pair, ranked by the count-weighted sum of their times per
+    product.  The caller measures the first few as real mixed launches."""
+    best = {}   # (n, S, threads) -> (ns per product, spec)
+    for r in records:
+        if r["n"] not in weights or abs(math.log2(r["batch"]) - math.log2(batch)) > 1.0:
+            continue
+        S = int(r["spec"].split("/")[1])
+        key = (r["n"], S, r["threads"])
+        ns = r["ms"] * 1e6 / r["batch"]
+        if key not in best or ns < best[key][0]:
+            best[key] = (ns, r["spec"])
+    pairs = {(S, t) for (_, S, t) in best}
+    scored = []
+    for S, t in pairs:
+        if all((n, S, t) in best for n in weights):
+            cost = sum(w * best[(n, S, t)][0] for n, w in weights.items())
+            scored.append((cost, {n: best[(n, S, t)][1] for n in weights}))
+    scored.sort(key=lambda x: x[0])
+    return [plans for _, plans in scored[:top]]
+
+
+PACKAGED_TIMING_LOG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans", "gb300_timing_log.jsonl.gz")
+
+
+def packaged_log() -> list:
+    """The GB300 timing log shipped with the package (exhaustive search over six sizes)."""
+    import gzip
+    with gzip.open(PACKAGED_TIMING_LOG, "rt") as f:
+        return [json.loads(line) for line in f if line.strip()]
+
+
 # ------------------------------------------------------------------ plan database
 # Text file read by the C library (gf2x_ctx_load_plan_db): one line
 # "n batch_bucket spec ms mults_per_s" per tuned (size, batch bucket).

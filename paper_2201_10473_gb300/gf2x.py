@@ -165,10 +165,17 @@ def _check_operand(t: torch.Tensor, n: int, name: str):
         raise ValueError(f"{name} must be contiguous with at least {limbs(n)} limbs in its last dimension")
 
 
-class Context:
-    """Owns a gf2x_ctx on one device."""
+PACKAGED_PLAN_DB = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans", "gb300_plan_db.txt")
 
-    def __init__(self, device: int | None = None):
+
+class Context:
+    """Owns a gf2x_ctx on one device.
+
+    plan_db: a plan database file to install ("packaged" = the GB300-tuned
+    database shipped with the package, None = the library's model-based
+    default plans); batch_hint selects its batch bucket."""
+
+    def __init__(self, device: int | None = None, plan_db: str | None = "packaged", batch_hint: int = 2048):
         if device is None:
             device = torch.cuda.current_device()
         self.device = device
@@ -177,6 +184,10 @@ class Context:
         if st:
             raise Gf2xError(st, "gf2x_ctx_create")
         self._h = h
+        if plan_db == "packaged":
+            plan_db = PACKAGED_PLAN_DB if os.path.exists(PACKAGED_PLAN_DB) else None
+        if plan_db:
+            self.load_plan_db(plan_db, batch_hint)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1,0 +1,310 @@
+"""Continuous-batching request loop for products in F2[X]/(X^n - 1).
+
+Requests (n, a, b) arrive over time with their operands already resident on
+the device.  The loop
+
+  * admits a request when an output slot of its size is free in a fixed HBM
+    budget (a device arena carved into per-size slots), else it waits;
+  * keeps up to `streams` batches in flight, one per CUDA stream; whenever a
+    stream is free it launches everything admitted so far (up to max_batch)
+    as ONE persistent launch over a device item array, replayed from a CUDA
+    graph captured per (stream, padded batch size);
+  * retires batches as their events complete, freeing their slots so that
+    waiting requests are admitted while other batches are still running.
+
+The plain baseline launches one product per request (one CTA each), on the
+same streams.  Latency is completion time (event observed by the loop)
+minus arrival time.
+"""
+from __future__ import annotations
+
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import gf2x
+
+
+@dataclass
+class RequestSet:
+    """Requests with device-resident operands, grouped by size."""
+    sizes: np.ndarray                 # n of request r
+    index: np.ndarray                 # row of request r in its size's operand tensors
+    a: dict = field(default_factory=dict)   # n -> (count_n, L) int64 CUDA tensor
+    b: dict = field(default_factory=dict)
+
+    def __len__(self):
+        return len(self.sizes)
+
+    def ptrs(self, rs: np.ndarray):
+        """Device addresses of the operands of requests rs."""
+        pa = np.empty(len(rs), dtype=np.int64)
+        pb = np.empty(len(rs), dtype=np.int64)
+        for n in np.unique(self.sizes[rs]):
+            sel = self.sizes[rs] == n
+            L = gf2x.limbs(int(n))
+            pa[sel] = self.a[int(n)].data_ptr() + self.index[rs[sel]] * 8 * L
+            pb[sel] = self.b[int(n)].data_ptr() + self.index[rs[sel]] * 8 * L
+        return pa, pb
+
+
+def make_requests(sizes, operand_fn) -> RequestSet:
+    """operand_fn(n, count) -> (a, b) numpy uint64 arrays of `count` rows."""
+    import torch
+    sizes = np.asarray(sizes, dtype=np.int64)
+    index = np.zeros(len(sizes), dtype=np.int64)
+    rs = RequestSet(sizes, index)
+    for n in np.unique(sizes):
+        sel = np.nonzero(sizes == n)[0]
+        index[sel] = np.arange(len(sel))
+        a, b = operand_fn(int(n), len(sel))
+        rs.a[int(n)] = torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+        rs.b[int(n)] = torch.from_numpy(np.ascontiguousarray(b).view(np.int64)).cuda()
+    return rs
+
+
+class SlotPool:
+    """Output slots of every size class carved from one arena of budget_bytes."""
+
+    def __init__(self, sizes: dict, budget_bytes: int):
+        import torch
+        total_w = sum(sizes.values())
+        self.arena = torch.empty(max(1, budget_bytes // 8), dtype=torch.int64, device="cuda")
+        base = self.arena.data_ptr()
+        self.free = {}
+        self.slot_limbs = {}
+        off = 0
+        for n, w in sorted(sizes.items()):
+            L = (gf2x.limbs(n) + 1) // 2 * 2           # 16-byte aligned slots
+            share = int(budget_bytes * w / total_w) // (8 * L)
+            self.slot_limbs[n] = L
+            self.free[n] = deque(base + 8 * (off + i * L) for i in range(share))
+            off += share * L
+        self.capacity = {n: len(q) for n, q in self.free.items()}
+
+    def take(self, n: int):
+        q = self.free.get(n)
+        return q.popleft() if q else None
+
+    def give(self, n: int, addr: int):
+        self.free[n].append(addr)
+
+
+@dataclass
+class ServeResult:
+    latency_s: np.ndarray
+    wall_s: float
+    completed: int
+    batches: int
+    mean_batch: float
+    max_inflight_seen: int
+    admission_waits: int
+
+    def summary(self) -> dict:
+        lat = self.latency_s
+        return {"completed": self.completed, "wall_s": self.wall_s,
+                "mults_per_s": self.completed / self.wall_s if self.wall_s > 0 else None,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3), "batches": self.batches, "mean_batch": self.mean_batch,
+                "admission_waits": self.admission_waits}
+
+
+class Server:
+    """Continuous batching over graph-captured persistent launches."""
+
+    def __init__(self, ctx: gf2x.Context, size_weights: dict, budget_bytes: int, max_batch: int = 2048,
+                 streams: int = 3, use_graphs: bool = True, min_bucket: int = 32):
+        import torch
+        self.torch = torch
+        self.ctx = ctx
+        self.max_batch = max_batch
+        self.nstreams = streams
+        self.use_graphs = use_graphs
+        ctx.prepare(sorted(size_weights))
+        self.pool = SlotPool(size_weights, budget_bytes)
+        self.streams = [torch.cuda.Stream() for _ in range(streams)]
+        self.items_host = [torch.zeros((max_batch, 4), dtype=torch.int64).pin_memory() for _ in range(streams)]
+        self.items_dev = [torch.zeros((max_batch, 4), dtype=torch.int64, device="cuda") for _ in range(streams)]
+        self.buckets = []
+        b = min_bucket
+        while b < max_batch:
+            self.buckets.append(b)
+            b *= 2
+        self.buckets.append(max_batch)
+        self.graphs = {}
+        if use_graphs:
+            self._capture()
+
+    def _launch(self, s: int, count: int):
+        torch = self.torch
+        self.items_dev[s][:count].copy_(self.items_host[s][:count], non_blocking=True)
+        self.ctx.mul_batched_device(self.items_dev[s], count, persistent=True, stream=torch.cuda.current_stream())
+
+    def _capture(self):
+        torch = self.torch
+        for s in range(self.nstreams):
+            self.items_host[s].zero_()          # empty slots: nothing to compute while capturing
+            with torch.cuda.stream(self.streams[s]):
+                self._launch(s, self.buckets[0])  # warm-up outside capture
+            torch.cuda.synchronize()
+            for B in self.buckets:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=self.streams[s]):
+                    self._launch(s, B)
+                self.graphs[(s, B)] = g
+        torch.cuda.synchronize()
+
+    def _bucket(self, k: int) -> int:
+        for b in self.buckets:
+            if b >= k:
+                return b
+        return self.buckets[-1]
+
+    def run(self, reqs: RequestSet, arrivals: np.ndarray, collect=None) -> ServeResult:
+        """Serve every request of `reqs`; arrivals[r] is its arrival time in
+        seconds from the start.  collect(r_array, addr_array, n) is called on
+        each retired batch (before its slots are reused) if given."""
+        torch = self.torch
+        N = len(reqs)
+        order = np.argsort(arrivals, kind="stable")
+        arr = arrivals[order]
+        queue = deque()
+        inflight = deque()        # (stream, event, reqs, addrs)
+        free_streams = deque(range(self.nstreams))
+        done_t = np.zeros(N)
+        nxt = 0
+        completed = 0
+        batches = 0
+        batch_sum = 0
+        waits = 0
+        max_inflight = 0
+        t0 = time.perf_counter()
+        while completed < N:
+            now = time.perf_counter() - t0
+            while nxt < N and arr[nxt] <= now:
+                queue.append(int(order[nxt]))
+                nxt += 1
+            progressed = False
+            while inflight and inflight[0][1].query():
+                s, ev, rs, addrs = inflight.popleft()
+                tdone = time.perf_counter() - t0
+                done_t[rs] = tdone
+                if collect is not None:
+                    collect(rs, addrs, reqs.sizes[rs])
+                for r, ad in zip(rs, addrs):
+                    self.pool.give(int(reqs.sizes[r]), int(ad))
+                completed += len(rs)
+                free_streams.append(s)
+                progressed = True
+            while free_streams and queue:
+                rs_l, addr_l = [], []
+                while queue and len(rs_l) < self.max_batch:
+                    r = queue[0]
+                    ad = self.pool.take(int(reqs.sizes[r]))
+                    if ad is None:           # no memory for the head request: wait for a retirement
+                        waits += 1
+                        break
+                    queue.popleft()
+                    rs_l.append(r)
+                    addr_l.append(ad)
+                if not rs_l:
+                    break
+                s = free_streams.popleft()
+                rs = np.array(rs_l, dtype=np.int64)
+                addrs = np.array(addr_l, dtype=np.int64)
+                pa, pb = reqs.ptrs(rs)
+                k = len(rs)
+                B = self._bucket(k) if self.use_graphs else k
+                h = self.items_host[s].numpy()
+                h[:k, 0] = pa
+                h[:k, 1] = pb
+                h[:k, 2] = addrs
+                h[:k, 3] = reqs.sizes[rs] | (1 << 32)      # n | GF2X_REDUCE << 32
+                h[k:B] = 0
+                with torch.cuda.stream(self.streams[s]):
+                    if self.use_graphs:
+                        self.graphs[(s, B)].replay()
+                    else:
+                        self._launch(s, k)
+                    ev = torch.cuda.Event()
+                    ev.record(self.streams[s])
+                inflight.append((s, ev, rs, addrs))
+                max_inflight = max(max_inflight, len(inflight))
+                batches += 1
+                batch_sum += k
+                progressed = True
+            if not progressed:
+                if inflight:
+                    time.sleep(2e-6)
+                elif nxt < N:
+                    time.sleep(max(0.0, min(1e-4, arr[nxt] - (time.perf_counter() - t0))))
+        wall = float(done_t.max() - arr[0]) if N else 0.0
+        return ServeResult(done_t - arrivals, wall, completed, batches, batch_sum / max(1, batches), max_inflight,
+                           waits)
+
+
+def serve_plain(ctx: gf2x.Context, reqs: RequestSet, arrivals: np.ndarray, pool: SlotPool, streams: int = 3,
+                collect=None) -> ServeResult:
+    """Baseline: one launch (one CTA) per request on arrival, round-robin over streams."""
+    import torch
+    N = len(reqs)
+    order = np.argsort(arrivals, kind="stable")
+    arr = arrivals[order]
+    ss = [torch.cuda.Stream() for _ in range(streams)]
+    inflight = deque()
+    pending = deque()
+    done_t = np.zeros(N)
+    nxt = 0
+    completed = 0
+    launches = 0
+    waits = 0
+    L = gf2x.lib()
+    t0 = time.perf_counter()
+    while completed < N:
+        now = time.perf_counter() - t0
+        while nxt < N and arr[nxt] <= now:
+            pending.append(int(order[nxt]))
+            nxt += 1
+        progressed = False
+        while inflight and inflight[0][0].query():
+            ev, r, ad = inflight.popleft()
+            done_t[r] = time.perf_counter() - t0
+            if collect is not None:
+                collect(np.array([r]), np.array([ad]), reqs.sizes[[r]])
+            pool.give(int(reqs.sizes[r]), ad)
+            completed += 1
+            progressed = True
+        while pending:
+            r = pending[0]
+            n = int(reqs.sizes[r])
+            ad = pool.take(n)
+            if ad is None:
+                waits += 1
+                break
+            pending.popleft()
+            pa, pb = reqs.ptrs(np.array([r]))
+            s = ss[launches % streams]
+            st = L.gf2x_mulmod_xn1(ctx._h, int(ad), int(pa[0]), int(pb[0]), n, gf2x.ctypes.c_void_p(s.cuda_stream))
+            if st:
+                raise gf2x.Gf2xError(st, "gf2x_mulmod_xn1")
+            ev = torch.cuda.Event()
+            ev.record(s)
+            inflight.append((ev, r, ad))
+            launches += 1
+            progressed = True
+        if not progressed:
+            if inflight:
+                time.sleep(2e-6)
+            elif nxt < N:
+                time.sleep(max(0.0, min(1e-4, arr[nxt] - (time.perf_counter() - t0))))
+    wall = float(done_t.max() - arr[0]) if N else 0.0
+    return ServeResult(done_t - arrivals, wall, completed, launches, 1.0, 0, waits)
+
+
+def default_budget(sizes, fraction_inflight: int) -> int:
+    """Bytes for `fraction_inflight` output slots of the average size."""
+    avg = sum(gf2x.limbs(n) for n in sizes) / len(sizes)
+    return int(math.ceil(fraction_inflight * avg * 8))
