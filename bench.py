@@ -49,8 +49,8 @@ WORKLOADS = {
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
-    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="hqc128")
     p.add_argument("--no-plain", action="store_true", help="skip the plain one-launch-per-product measurement")
@@ -137,24 +137,26 @@ def cpu_cores() -> int:
 # ---------------------------------------------------------------- oracle legs
 
 def oracle_rate(w: dict, seconds: float, first_product: int = 0) -> dict:
-    """The oracle as it stands on the host cores over a bounded sample."""
+    """The oracle as it stands, on all host cores, over a bounded sample:
+    chunks of the workload's products until about `seconds` have passed."""
     import oracle
     n, reduce = w["n"], w["reduce"]
     cores = cpu_cores()
     seed = wl.BASE_SEED + w["key"]
-    # size the sample from one timed product
-    a1, b1 = wl.dense_pair(seed, n, 1, first=first_product)
+    chunk = min(w["batch"], 4 * cores)
+    a, b = wl.dense_pair(seed, n, chunk, first=first_product)
+    oracle.mul_batch(a[:cores], b[:cores], n, reduce=reduce, nthreads=cores)      # warm-up
+    done = 0
     t0 = time.perf_counter()
-    oracle.mul_batch(a1, b1, n, reduce=reduce, nthreads=1)
-    one = max(time.perf_counter() - t0, 1e-4)
-    count = int(max(cores, min(w["batch"], seconds * cores / one)))
-    a, b = wl.dense_pair(seed, n, count, first=first_product)
-    t0 = time.perf_counter()
-    oracle.mul_batch(a, b, n, reduce=reduce, nthreads=cores)
-    dt = time.perf_counter() - t0
-    return {"value": count / dt, "unit": "mults/s", "cores": cores, "kind": "oracle",
-            "sample": f"{count} of the workload's {w['batch']} products (n={n}, seed {seed}), "
-                      f"oracle_mul_batch on {cores} threads, {dt:.2f} s"}
+    while True:
+        oracle.mul_batch(a, b, n, reduce=reduce, nthreads=cores)
+        done += chunk
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    return {"value": done / dt, "unit": "mults/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} products ({chunk} distinct of the workload, n={n}, seed {seed}) in {dt:.1f} s, "
+                      f"oracle_mul_batch on {cores} threads"}
 
 
 def run_reference(args, w):

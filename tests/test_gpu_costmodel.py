@@ -86,3 +86,15 @@ def test_training_fits_a_known_function():
         _call("gf2x_mlp_adam", m.params.data_ptr(), G.data_ptr(), M.data_ptr(), V.data_ptr(), m.np,
               ctypes.c_float(3e-3), ctypes.c_float(0.9), ctypes.c_float(0.999), ctypes.c_float(1e-8), step, s)
     assert L.item() < 0.02 * first
+
+
+@pytest.mark.parametrize("holdout", [17669, 57637])
+def test_learned_model_beats_unguided_search(holdout):
+    """Trained by the CUDA kernels on the GB300 timing log of the other sizes,
+    the network orders the held-out size's candidates so that a plan within 5%
+    of the exhaustive best comes far earlier than in random order, and its top
+    10 are within 10% of the best (exhaustive search is the judge)."""
+    from paper_2201_10473_gb300 import autotune, costmodel
+    r = costmodel.evaluate_gain(autotune.packaged_log(), holdout, 2048, k=10, steps=3000)
+    assert r["model_measurements_to_5pct"] * 4 <= r["random_expected_measurements_to_5pct"], r
+    assert r["regret_top_k"] <= 0.10, r
