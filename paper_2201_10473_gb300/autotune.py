@@ -293,7 +293,13 @@ def main(argv=None):
     p.add_argument("--budget", type=float, default=None, help="seconds per (size, batch) search")
     p.add_argument("--limit", type=int, default=None)
     p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--from-log", default=None, help="re-measure only the best --top plans of this timing log "
+                                                     "('packaged' = the shipped GB300 log)")
+    p.add_argument("--top", type=int, default=60)
     a = p.parse_args(argv)
+    prior = None
+    if a.from_log:
+        prior = packaged_log() if a.from_log == "packaged" else read_log(a.from_log)
     db = load_db(a.db)
     rng = random.Random(a.seed)
     sizes = [int(x) for x in a.sizes.split(",") if x]
@@ -302,6 +308,9 @@ def main(argv=None):
         ctx = gf2x.Context()          # a fresh plan table per size
         tuner = Autotuner(ctx, a.log)
         cands = candidate_specs(n, limit=a.limit)
+        if prior is not None:
+            ranked = sorted((r for r in prior if r["n"] == n and r["batch"] == batches[0]), key=lambda r: r["ms"])
+            cands = list(dict.fromkeys(r["spec"] for r in ranked))[: a.top] or cands
         t0 = time.time()
         res = tuner.search(n, batches[0], cands, a.budget)
         if not res:

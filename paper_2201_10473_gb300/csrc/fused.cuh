@@ -46,19 +46,31 @@ __device__ __forceinline__ uint32_t mul_hi_s(uint32_t a, uint32_t b)
     return d;
 }
 
+// Words of the accumulator shift done on the ALU pipe (funnel shift, 1 op)
+// instead of the FMA pipe (mul.hi + mad.lo, 3 issue units: mul.hi runs at half
+// rate), chosen so that per bit position the ALU load S^2 + x balances the
+// FMA load 3(2S - x) + 3S of the remaining shifts and the masks.
+template <int S>
+struct CombSplit {
+    static constexpr int v = (9 * S - S * S) / 4;
+    static constexpr int kAluShift = v < 0 ? 0 : (v > 2 * S ? 2 * S : v);
+};
+
 // S x S-word carry-less product by the comb method, in registers: for every
 // bit position j (high to low) of the 32-bit words of b, shift the
 // accumulator left by one and XOR a into word i of it wherever bit j of b[i]
 // is set (AND with the sign-extended bit: no branch).  This replaces the
 // paper's Mult64 (Sec. 2.1, PCLMULQDQ), which the GPU does not have.
 //   FMA = false: shifts and masks on the ALU pipe (SHF), 32 (S^2 + 4S) ALU ops.
-//   FMA = true : the accumulator shift (c = 2c + hi(2 c_prev)) and the masks
-//                (m = hi_signed(2 b), b = 2b) are IMADs on the FMA pipe; the
-//                ALU pipe only runs the 32 S^2 AND-XORs.
+//   FMA = true : the masks (m = hi_signed(2 b), b = 2b) and part of the
+//                accumulator shift (c = 2c + hi(2 c_prev)) are IMADs on the FMA
+//                pipe, the rest of the shift is funnel shifts (CombSplit), and
+//                the ALU pipe runs the 32 S^2 AND-XORs.
 // b is consumed.
 template <int S, bool FMA>
 __device__ __forceinline__ void comb(const uint32_t (&a)[S], uint32_t (&b)[S], uint32_t (&c)[2 * S], uint32_t two)
 {
+    constexpr int kAlu = FMA ? CombSplit<S>::kAluShift : 2 * S;
 #pragma unroll
     for (int i = 0; i < 2 * S; ++i)
         c[i] = 0u;
@@ -66,7 +78,7 @@ __device__ __forceinline__ void comb(const uint32_t (&a)[S], uint32_t (&b)[S], u
     for (int j = 0; j < 32; ++j) {
 #pragma unroll
         for (int k = 2 * S - 1; k > 0; --k)
-            c[k] = FMA ? mad_lo(c[k], two, mul_hi_u(c[k - 1], two)) : __funnelshift_l(c[k - 1], c[k], 1);
+            c[k] = (k <= kAlu) ? __funnelshift_l(c[k - 1], c[k], 1) : mad_lo(c[k], two, mul_hi_u(c[k - 1], two));
         c[0] = FMA ? mul_lo(c[0], two) : (c[0] << 1);
 #pragma unroll
         for (int i = 0; i < S; ++i) {
