@@ -189,9 +189,11 @@ gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, co
  *    a reused buffer is first waited for on the host).  Items whose plans
  *    share a leaf size run in one launch (one launch per leaf size).
  *  - GF2X_BATCH_ITEMS_ON_DEVICE: `items` is a device array of gf2x_item read
- *    by the kernel, which looks each plan up by n on the device; every n
- *    must have been prepared (gf2x_ctx_prepare) and all prepared plans must
- *    share one leaf size (else GF2X_EUNSUPPORTED).  An item whose n has no
+ *    by the kernel, which looks each plan up by n on the device among the
+ *    sizes of the last gf2x_ctx_prepare call; those plans must share one
+ *    leaf size (else GF2X_EUNSUPPORTED).  The launch gets the largest CTA and
+ *    shared memory of those plans; a plan that does not match the launch is
+ *    refused on the device and reported (never run).  An item whose n has no
  *    plan is skipped and reported by gf2x_ctx_sync_status; an item with
  *    n = 0 is an empty slot, skipped silently (padding for fixed-size
  *    captured launches).  Nothing is
@@ -204,8 +206,10 @@ gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, size_t count
                              uint32_t batch_flags, gf2x_stream stream);
 
 /* Build and upload (synchronously on `stream`) the current plans of the
- * given sizes, so that later calls, device-item batches and CUDA graph
- * captures find them ready. */
+ * given sizes, so that later calls and CUDA graph captures find them ready,
+ * and make exactly these sizes the ones device-item batches accept (their
+ * plans are looked up by n on the device; other sizes are reported as
+ * having no plan). */
 gf2x_status gf2x_ctx_prepare(gf2x_ctx *ctx, const uint32_t *sizes, size_t count, gf2x_stream stream);
 
 /* Launch shape the context uses for size n: CTA threads, dynamic shared

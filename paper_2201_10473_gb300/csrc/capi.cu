@@ -59,6 +59,7 @@ struct gf2x_ctx {
     std::vector<uint32_t> scratch_S;
     std::unordered_map<std::string, uint32_t> slot_of;  // (n, spec, checked) -> plan slot, for reuse
     std::unordered_map<uint64_t, int> occupancy;        // (leaf, threads, smem) -> resident CTAs per SM
+    std::vector<uint32_t> device_set;                   // sizes of device-item batches (last gf2x_ctx_prepare)
 };
 
 static std::string plan_key(uint32_t n, const gf2x_plan_spec &spec, int checked)
@@ -244,7 +245,12 @@ static gf2x_status plan_for(gf2x_ctx *ctx, uint32_t n, cudaStream_t stream, uint
         return st;
     map[n] = PlanEntry{s, spec};
     *slot = s;
-    return publish_plan(ctx, n, s, stream);
+    return GF2X_OK;
+}
+
+static bool in_device_set(const gf2x_ctx *ctx, uint32_t n)
+{
+    return std::find(ctx->device_set.begin(), ctx->device_set.end(), n) != ctx->device_set.end();
 }
 
 extern "C" gf2x_status gf2x_ctx_set_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_plan_spec *spec)
@@ -257,8 +263,16 @@ extern "C" gf2x_status gf2x_ctx_set_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_p
     ctx->by_n.erase(n);
     ctx->by_n_checked.erase(n);
     if (!spec) {
-        ctx->plan_of_n_host[n] = kNoPlan;
-        cudaMemcpy(ctx->plan_of_n_dev + n, ctx->plan_of_n_host + n, sizeof(uint32_t), cudaMemcpyHostToDevice);
+        if (in_device_set(ctx, n)) {
+            uint32_t slot;
+            gf2x_status st = plan_for(ctx, n, nullptr, &slot);
+            if (st != GF2X_OK)
+                return st;
+            st = publish_plan(ctx, n, slot, nullptr);
+            if (st != GF2X_OK)
+                return st;
+            cudaStreamSynchronize(nullptr);
+        }
         return GF2X_OK;
     }
     gf2x_plan_info info;
@@ -270,9 +284,11 @@ extern "C" gf2x_status gf2x_ctx_set_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_p
     if (st != GF2X_OK)
         return st;
     (ctx->checked ? ctx->by_n_checked : ctx->by_n)[n] = PlanEntry{s, *spec};
-    st = publish_plan(ctx, n, s, nullptr);
-    if (st != GF2X_OK)
-        return st;
+    if (in_device_set(ctx, n)) {
+        st = publish_plan(ctx, n, s, nullptr);
+        if (st != GF2X_OK)
+            return st;
+    }
     cudaError_t e = cudaStreamSynchronize(nullptr);
     return e == cudaSuccess ? GF2X_OK : cuda_fail(ctx, e, "plan upload");
 }
@@ -301,6 +317,17 @@ extern "C" gf2x_status gf2x_ctx_set_checked(gf2x_ctx *ctx, int on)
     if (!ctx)
         return GF2X_EINVAL;
     ctx->checked = on ? 1 : 0;
+    // device-item batches follow the mode: republish the prepared sizes' plans
+    for (uint32_t n : ctx->device_set) {
+        uint32_t slot;
+        gf2x_status st = plan_for(ctx, n, nullptr, &slot);
+        if (st != GF2X_OK)
+            return st;
+        st = publish_plan(ctx, n, slot, nullptr);
+        if (st != GF2X_OK)
+            return st;
+    }
+    cudaStreamSynchronize(nullptr);
     return GF2X_OK;
 }
 
@@ -493,14 +520,17 @@ extern "C" gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, s
     if (batch_flags & GF2X_BATCH_ITEMS_ON_DEVICE) {
         // one launch over the caller's device array; plans are looked up by n
         // on the device, so every size must have been prepared beforehand
-        auto &map = ctx->checked ? ctx->by_n_checked : ctx->by_n;
-        if (map.empty())
+        if (ctx->device_set.empty())
             return fail(ctx, GF2X_EINVAL, "no prepared sizes: call gf2x_ctx_prepare first");
         uint32_t S = 0;
         unsigned threads = 0;
         uint32_t smem_words = 0;
-        for (auto &kv : map) {
-            const GPlan &P = ctx->plans_host[kv.second.slot];
+        for (uint32_t n : ctx->device_set) {
+            uint32_t slot;
+            gf2x_status st = plan_for(ctx, n, s, &slot);
+            if (st != GF2X_OK)
+                return st;
+            const GPlan &P = ctx->plans_host[slot];
             if (S && P.S != S)
                 return fail(ctx, GF2X_EUNSUPPORTED, "device item batches need one leaf size over the prepared plans");
             S = P.S;
@@ -622,11 +652,28 @@ extern "C" gf2x_status gf2x_ctx_prepare(gf2x_ctx *ctx, const uint32_t *sizes, si
     if (!ctx || (count && !sizes))
         return GF2X_EINVAL;
     cudaSetDevice(ctx->device);
-    for (size_t i = 0; i < count; ++i) {
-        uint32_t slot;
-        gf2x_status st = plan_for(ctx, sizes[i], (cudaStream_t)stream, &slot);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<uint32_t> next(sizes, sizes + count);
+    for (uint32_t n : next)
+        if (n < 1 || n > GF2X_MAX_N)
+            return fail(ctx, GF2X_EUNSUPPORTED, "n outside [1, 131072]");
+    // withdraw the previous device set, then publish the new one
+    for (uint32_t n : ctx->device_set) {
+        gf2x_status st = publish_plan(ctx, n, kNoPlan, s);
         if (st != GF2X_OK)
             return st;
+    }
+    ctx->device_set.clear();
+    for (uint32_t n : next) {
+        uint32_t slot;
+        gf2x_status st = plan_for(ctx, n, s, &slot);
+        if (st != GF2X_OK)
+            return st;
+        st = publish_plan(ctx, n, slot, s);
+        if (st != GF2X_OK)
+            return st;
+        if (!in_device_set(ctx, n))
+            ctx->device_set.push_back(n);
     }
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     return e == cudaSuccess ? GF2X_OK : cuda_fail(ctx, e, "prepare");

@@ -18,59 +18,17 @@ __device__ __forceinline__ uint32_t fdiv(const FastDiv &f, uint32_t x)
 }
 
 // ---------------------------------------------------------------- leaf
-// Integer helpers that keep work on the FMA pipe: the multiplier `two` (= 2)
-// is read from memory, so these stay IMADs instead of being turned into
-// shifts on the ALU pipe, which the AND-XOR operations already fill.
-__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
-{
-    uint32_t d;
-    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-}
-__device__ __forceinline__ uint32_t mul_lo(uint32_t a, uint32_t b)
-{
-    uint32_t d;
-    asm("mul.lo.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-__device__ __forceinline__ uint32_t mul_hi_u(uint32_t a, uint32_t b)
-{
-    uint32_t d;
-    asm("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-__device__ __forceinline__ uint32_t mul_hi_s(uint32_t a, uint32_t b)
-{
-    uint32_t d;
-    asm("mul.hi.s32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-
-// Words of the accumulator shift done on the ALU pipe (funnel shift, 1 op)
-// instead of the FMA pipe (mul.hi + mad.lo, 3 issue units: mul.hi runs at half
-// rate), chosen so that per bit position the ALU load S^2 + x balances the
-// FMA load 3(2S - x) + 3S of the remaining shifts and the masks.
-template <int S>
-struct CombSplit {
-    static constexpr int v = (9 * S - S * S) / 4;
-    static constexpr int kAluShift = v < 0 ? 0 : (v > 2 * S ? 2 * S : v);
-};
-
 // S x S-word carry-less product by the comb method, in registers: for every
-// bit position j (high to low) of the 32-bit words of b, shift the
-// accumulator left by one and XOR a into word i of it wherever bit j of b[i]
-// is set (AND with the sign-extended bit: no branch).  This replaces the
-// paper's Mult64 (Sec. 2.1, PCLMULQDQ), which the GPU does not have.
-//   FMA = false: shifts and masks on the ALU pipe (SHF), 32 (S^2 + 4S) ALU ops.
-//   FMA = true : the masks (m = hi_signed(2 b), b = 2b) and part of the
-//                accumulator shift (c = 2c + hi(2 c_prev)) are IMADs on the FMA
-//                pipe, the rest of the shift is funnel shifts (CombSplit), and
-//                the ALU pipe runs the 32 S^2 AND-XORs.
-// b is consumed.
-template <int S, bool FMA>
-__device__ __forceinline__ void comb(const uint32_t (&a)[S], uint32_t (&b)[S], uint32_t (&c)[2 * S], uint32_t two)
+// bit position j (high to low) of the 32-bit words of b, shift the 2S-word
+// accumulator left by one (funnel shifts) and XOR a into word i of it
+// wherever bit j of b[i] is set (AND with the sign-extended bit: no branch).
+// 32 (S^2 + 4S) integer operations for (32S)^2 bit products.  This replaces
+// the paper's Mult64 (Sec. 2.1, PCLMULQDQ), which the GPU does not have.
+// (Moving the shifts and masks to the FMA pipe with mul.hi/mad.lo measured
+// slower on GB300: mul.hi issues at half rate.)  b is consumed.
+template <int S>
+__device__ __forceinline__ void comb(const uint32_t (&a)[S], uint32_t (&b)[S], uint32_t (&c)[2 * S])
 {
-    constexpr int kAlu = FMA ? CombSplit<S>::kAluShift : 2 * S;
 #pragma unroll
     for (int i = 0; i < 2 * S; ++i)
         c[i] = 0u;
@@ -78,12 +36,12 @@ __device__ __forceinline__ void comb(const uint32_t (&a)[S], uint32_t (&b)[S], u
     for (int j = 0; j < 32; ++j) {
 #pragma unroll
         for (int k = 2 * S - 1; k > 0; --k)
-            c[k] = (k <= kAlu) ? __funnelshift_l(c[k - 1], c[k], 1) : mad_lo(c[k], two, mul_hi_u(c[k - 1], two));
-        c[0] = FMA ? mul_lo(c[0], two) : (c[0] << 1);
+            c[k] = __funnelshift_l(c[k - 1], c[k], 1);
+        c[0] <<= 1;
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-            const uint32_t m = FMA ? mul_hi_s(b[i], two) : (uint32_t)((int32_t)b[i] >> 31);
-            b[i] = FMA ? mul_lo(b[i], two) : (b[i] << 1);
+            const uint32_t m = (uint32_t)((int32_t)b[i] >> 31);
+            b[i] <<= 1;
 #pragma unroll
             for (int k = 0; k < S; ++k)
                 c[i + k] ^= a[k] & m;
@@ -111,26 +69,26 @@ __device__ __forceinline__ void store_words(uint32_t *p, const uint32_t (&r)[N])
 }
 
 // Leaf slot: A (S words) then B (S words); the 2S-word product replaces them.
-template <int S, bool FMA>
-__device__ __forceinline__ void leaf_plain(uint32_t *slot, uint32_t two)
+template <int S>
+__device__ __forceinline__ void leaf_plain(uint32_t *slot)
 {
     uint32_t a[S], b[S], c[2 * S];
     load_words<S>(a, slot);
     load_words<S>(b, slot + S);
-    comb<S, FMA>(a, b, c, two);
+    comb<S>(a, b, c);
     store_words<2 * S>(slot, c);
 }
 
 // Leaf slot of a 2-way Karatsuba node (Alg. 1, one level): A = A0 + X^{32S} A1,
 // B likewise (2S words each); R = R0 + (R0 + R1 + R2) X^{32S} + R1 X^{64S}
 // with R0 = A0 B0, R1 = A1 B1, R2 = (A0 + A1)(B0 + B1), all in registers.
-template <int S, bool FMA>
-__device__ __forceinline__ void leaf_k2(uint32_t *slot, uint32_t two)
+template <int S>
+__device__ __forceinline__ void leaf_k2(uint32_t *slot)
 {
     uint32_t C[4 * S], r[2 * S], a[S], b[S];
     load_words<S>(a, slot);
     load_words<S>(b, slot + 2 * S);
-    comb<S, FMA>(a, b, r, two);
+    comb<S>(a, b, r);
 #pragma unroll
     for (int k = 0; k < 2 * S; ++k)
         C[k] = r[k];
@@ -142,7 +100,7 @@ __device__ __forceinline__ void leaf_k2(uint32_t *slot, uint32_t two)
         C[S + k] ^= r[k];
     load_words<S>(a, slot + S);
     load_words<S>(b, slot + 3 * S);
-    comb<S, FMA>(a, b, r, two);
+    comb<S>(a, b, r);
 #pragma unroll
     for (int k = 0; k < 2 * S; ++k) {
         C[2 * S + k] ^= r[k];
@@ -160,7 +118,7 @@ __device__ __forceinline__ void leaf_k2(uint32_t *slot, uint32_t two)
             b[k] ^= b1[k];
         }
     }
-    comb<S, FMA>(a, b, r, two);
+    comb<S>(a, b, r);
 #pragma unroll
     for (int k = 0; k < 2 * S; ++k)
         C[S + k] ^= r[k];
@@ -170,15 +128,14 @@ __device__ __forceinline__ void leaf_k2(uint32_t *slot, uint32_t two)
 template <int S>
 __device__ __forceinline__ void leaf_pass(const GPlan &P, uint32_t *base, uint32_t nleaf)
 {
-    const uint32_t two = P.two;
     if (P.fuse_k2) {
         if constexpr (S <= 10) {
             for (uint32_t l = threadIdx.x; l < nleaf; l += blockDim.x)
-                leaf_k2<S, true>(base + l * (4u * S), two);
+                leaf_k2<S>(base + l * (4u * S));
         }
     } else {
         for (uint32_t l = threadIdx.x; l < nleaf; l += blockDim.x)
-            leaf_plain<S, true>(base + l * (2u * S), two);
+            leaf_plain<S>(base + l * (2u * S));
     }
 }
 
@@ -550,7 +507,7 @@ __device__ void run_product(const GPlan &P, const DevItem &it, uint32_t *sm, uin
     const uint32_t ne = nlev - P.fuse_k2;   // levels run as shared-memory passes
     if (nlev == 0) {
         if (threadIdx.x == 0)
-            leaf_plain<S, true>(top, P.two);
+            leaf_plain<S>(top);
         __syncthreads();
     } else {
         uint32_t *leaf_base = sm + (P.fuse_k2 ? P.lev[nlev - 1].in_off : P.lev[nlev - 1].ch_off);
@@ -618,12 +575,20 @@ struct LeafTraits {
     static constexpr int kMaxThreads = S <= 6 ? 768 : 512;
 };
 
+__device__ __forceinline__ uint32_t dynamic_smem_bytes()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
 template <int S>
 __global__ void __launch_bounds__(LeafTraits<S>::kMaxThreads, 1)
 fused_mul_kernel(const LaunchArgs args)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ GPlan P;
+    const uint32_t smem_avail = dynamic_smem_bytes();
     const uint32_t step = args.persistent ? gridDim.x : args.count;
     for (uint32_t i = blockIdx.x; i < args.count; i += step) {
         const DevItem it = fetch_item(args, i);
@@ -640,6 +605,13 @@ fused_mul_kernel(const LaunchArgs args)
                 dst[w] = __ldg(src + w);
         }
         __syncthreads();
+        // a plan made for another leaf size or more shared memory than this
+        // launch has is refused (uniform over the CTA), never run
+        if (P.S != (uint32_t)S || 4u * P.smem_words > smem_avail || P.nlev > (uint32_t)kMaxLevels) {
+            if (threadIdx.x == 0)
+                flag_error(args.err, kErrPlanMismatch);
+            continue;
+        }
         run_product<S>(P, it, sm, args.err);
     }
 }

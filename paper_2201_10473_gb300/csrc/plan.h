@@ -65,7 +65,7 @@ struct GPlan {
     uint32_t part_words;
     uint32_t checked;    // verify exactness invariants on the device
     uint32_t fuse_k2;    // 1: the last level is a 2-way Karatsuba done inside the leaf thread
-    uint32_t two;        // the constant 2, read from memory so that multiplications by it stay IMADs
+    uint32_t reserved;
     uint32_t pad2_;
     GLevel lev[kMaxLevels];
 };
@@ -101,6 +101,6 @@ constexpr uint32_t kNoPlan = 0xffffffffu;
 constexpr uint32_t kEmptyItem = 0xfffffffeu;  // device item with n = 0: a padding slot, skipped
 
 // Checked-mode error codes (bit flags, OR-ed into *err).
-enum : uint32_t { kErrDivX = 1, kErrDivX1 = 2, kErrPad = 4, kErrNoPlan = 8 };
+enum : uint32_t { kErrDivX = 1, kErrDivX1 = 2, kErrPad = 4, kErrNoPlan = 8, kErrPlanMismatch = 16 };
 
 }  // namespace gf2x

@@ -197,7 +197,6 @@ gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec_in, GPlan *out, gf
     P.S = S;
     P.seq_top = s.seq_top;
     P.fuse_k2 = s.fuse_leaf;
-    P.two = 2;
     // depth of the deepest data held in shared memory (the fused level stays in registers)
     const uint32_t deepest = s.nlev - s.fuse_leaf;
 

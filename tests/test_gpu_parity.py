@@ -234,7 +234,7 @@ def test_sparse_weight_131_through_dense_path(ctx, n):
 
 def _device_item_ctx():
     from paper_2201_10473_gb300 import Context
-    c2 = Context(0)
+    c2 = Context(0, plan_db=None)
     plans = {17669: "T2.K3.K2.K2.K2/8", 35851: "T2.K3.K2.K2.K2.K2/8/0/1", 57637: "T16.K5.K2.K2.K2.K2/8/0/1"}
     for n, s in plans.items():
         c2.set_plan(n, s)
@@ -302,5 +302,37 @@ def test_device_item_without_plan_is_reported():
             c2.sync_status()
         assert e.value.status == 7
         c2.sync_status()   # the report is cleared
+    finally:
+        c2.close()
+
+
+def test_replayed_graph_refuses_a_plan_changed_under_it():
+    """A graph captured for one leaf size, replayed after the size's plan was
+    switched to another leaf: the kernel refuses the item and reports it,
+    instead of running a plan it was not built for."""
+    from paper_2201_10473_gb300 import Gf2xError, pack_items
+    from paper_2201_10473_gb300 import Context
+    c2 = Context(0, plan_db=None)
+    try:
+        n = 17669
+        c2.set_plan(n, "T2.K3.K2.K2.K2/8")
+        c2.prepare([n])
+        a, b = wl.dense_pair(5500, n, 2)
+        da, db = to_dev(a), to_dev(b)
+        o = torch.zeros((2, wl.limbs(n)), dtype=torch.int64, device="cuda")
+        items = pack_items([(da[i].data_ptr(), db[i].data_ptr(), o[i].data_ptr(), n, 1) for i in range(2)]).cuda()
+        c2.mul_batched_device(items, 2)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            c2.mul_batched_device(items, 2)
+        c2.set_plan(n, "T2.K2.K2.K2.K2.K2/6")      # another leaf size, published for device items
+        o.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        with pytest.raises(Gf2xError) as e:
+            c2.sync_status()
+        assert e.value.status == 7
+        assert int(o.abs().sum()) == 0               # nothing was written
     finally:
         c2.close()
