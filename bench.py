@@ -209,6 +209,32 @@ def config_of(w, spec, shape):
 
 # ---------------------------------------------------------------- our arm
 
+def kernel_source_hash() -> str:
+    """Hash of the fused kernel's source: traffic counters apply only to this version."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("fused.cuh", "plan.h"):
+        with open(os.path.join(ROOT, "paper_2201_10473_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, spec: str):
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.txt:
+    "workload plan kernel_source_hash dram_bytes_per_launch"), or None if the
+    kernel or the plan changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
+            for line in f:
+                parts = line.split("#", 1)[0].split()
+                if len(parts) == 4 and parts[0] == workload and parts[1] == spec and parts[2] == kernel_source_hash():
+                    return float(parts[3])
+    except OSError:
+        pass
+    return None
+
+
+
 def run_ours(args, w):
     import torch
     import torch.distributed as dist
@@ -352,13 +378,7 @@ def run_ours(args, w):
     ops_per_launch = info["ops_full"] * batch
     achieved = ops_per_launch / (mean_launch_ms * 1e-3) / 1e12
     peak = SMS * ALU_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = None
-    try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        key = f"{w['name']}|{spec}"
-        traffic = prof.get(key)
-    except (OSError, ValueError):
-        traffic = None
+    traffic = measured_traffic(w["name"], spec)
     observed = clk.get("sm_mhz")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
             "traffic": traffic,
