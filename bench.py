@@ -121,10 +121,8 @@ class ClockSampler:
 # ---------------------------------------------------------------- distributed
 
 def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2201_10473_gb300 import shard
+    return shard.world_info()
 
 
 def cpu_cores() -> int:
@@ -252,11 +250,14 @@ def run_ours(args, w):
     info = plan_info(n, spec)
     shape = ctx.launch_shape(n)
 
-    # input sets: rank r uses products r*batch .. (r+1)*batch-1 of the seeded stream;
-    # rotate R sets so the inputs touched between two uses exceed L2
+    # input sets: rank r multiplies products r*batch .. (r+1)*batch-1 of the seeded
+    # stream (weak scaling); rotate R copies so the inputs touched between two
+    # uses exceed L2
+    from paper_2201_10473_gb300 import shard
+    mine = shard.shard_range(rank, world, batch)
     in_bytes = 2 * batch * wl.limbs(n) * 8
     R = max(2, int(np.ceil(160e6 / in_bytes)))
-    host_a, host_b = wl.dense_pair(seed, n, batch, first=rank * batch)
+    host_a, host_b = wl.dense_pair(seed, n, batch, first=mine.start)
     sets = []
     for r in range(R):
         # every set is the same products (identical results); rotating copies defeat L2 reuse
@@ -308,11 +309,8 @@ def run_ours(args, w):
     total_ms = t_start.elapsed_time(t_end)
     clk = clocks.stop()
     launch_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * batch * K / (total_ms * 1e-3)
+    total_ms = shard.max_over_ranks(total_ms, device="cuda")
+    value = shard.whole_job_rate(batch * K, world, total_ms * 1e-3)
 
     # ---- end to end through the public API with host buffers
     pin_a = torch.from_numpy(host_a.view(np.int64)).pin_memory()
@@ -341,12 +339,9 @@ def run_ours(args, w):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = shard.max_over_ranks(e2e_ms, device="cuda")
     got_e2e = pin_out.numpy().view(np.uint64)
-    e2e_value = world * batch * K2 / (e2e_ms * 1e-3)
+    e2e_value = shard.whole_job_rate(batch * K2, world, e2e_ms * 1e-3)
 
     # ---- plain form: one launch of one CTA per product
     plain = None
@@ -616,6 +611,12 @@ def run_c5(device, requests):
         arr = wl.poisson_arrivals(wk.seed + int(f * 100), len(sizes), f * cap)
         r = srv.run(reqs, arr)
         out["loads"][str(f)] = dict(r.summary(), offered_per_s=f * cap)
+    # a tight budget (4 MiB of output slots): admission has to wait for retirements
+    tight = serve.Server(ctx, weights, 4 << 20, max_batch=2048, streams=3, use_graphs=True)
+    arr = wl.poisson_arrivals(wk.seed + 95, len(sizes), 0.95 * cap)
+    r = tight.run(reqs, arr)
+    out["tight_budget_4MiB_load_0.95"] = dict(r.summary(), offered_per_s=0.95 * cap,
+                                            slots=sum(tight.pool.capacity.values()))
     ctx.sync_status()
     # plain per-request launches on a subset
     m = min(4000, len(sizes))
