@@ -78,6 +78,12 @@ typedef enum {
  *   fuse_leaf: 1 = the last level (a 2-way Karatsuba) runs inside the leaf
  *            thread, in registers (leaf_words <= 10); 0 = it runs as a
  *            shared-memory level like the others.
+ *   split_top: 1 = the top level runs across CTAs: one kernel evaluates the
+ *            children into global scratch, the children are multiplied as
+ *            independent products (levels 1.. of the plan, where seq_top then
+ *            applies), and one kernel interpolates; for sizes whose whole tree
+ *            does not fit one CTA's shared memory (up to GF2X_MAX_N).  The
+ *            child size must be an even number of words.
  */
 typedef struct {
     uint32_t nlev;
@@ -87,6 +93,7 @@ typedef struct {
     uint32_t threads;
     uint32_t seq_top;
     uint32_t fuse_leaf;
+    uint32_t split_top;
 } gf2x_plan_spec;
 
 /* Facts about a plan for one n (host-side only, needs no GPU). */
@@ -104,6 +111,7 @@ typedef struct {
     uint64_t bytes_in;           /* HBM bytes read per product */
     uint64_t bytes_out_full;     /* HBM bytes written, full product */
     uint64_t bytes_out_reduced;  /* HBM bytes written, reduced product */
+    uint64_t scratch_bytes;      /* global scratch per product (split plans; 0 otherwise) */
 } gf2x_plan_info;
 
 /* Item of a batched call.  Pointers as in the conventions above. */
@@ -132,9 +140,9 @@ gf2x_status gf2x_default_spec(uint32_t n, gf2x_plan_spec *spec);
  * n or does not fit in one CTA's shared memory. */
 gf2x_status gf2x_plan_info_get(uint32_t n, const gf2x_plan_spec *spec, gf2x_plan_info *info);
 
-/* Parse a plan spec from text "T2.K3.K2.K2/8/288/0/1" (levels / leaf_words /
- * threads / seq_top / fuse_leaf; the last four fields optional, 0 =
- * automatic or off). */
+/* Parse a plan spec from text "T2.K3.K2.K2/8/288/0/1/0" (levels / leaf_words /
+ * threads / seq_top / fuse_leaf / split_top; the last five fields optional,
+ * 0 = automatic or off). */
 gf2x_status gf2x_spec_parse(const char *text, gf2x_plan_spec *spec);
 
 /* Create a context on CUDA device `device` (made current on the calling

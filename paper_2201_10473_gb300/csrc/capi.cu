@@ -30,6 +30,8 @@ struct PlanEntry {
     gf2x_plan_spec spec;
 };
 
+constexpr uint64_t kWorkspaceCap = 256ull << 20;  // split plans run in chunks of at most this much scratch
+
 struct Staging {
     DevItem *host = nullptr;   // pinned
     DevItem *dev = nullptr;
@@ -60,6 +62,12 @@ struct gf2x_ctx {
     std::unordered_map<std::string, uint32_t> slot_of;  // (n, spec, checked) -> plan slot, for reuse
     std::unordered_map<uint64_t, int> occupancy;        // (leaf, threads, smem) -> resident CTAs per SM
     std::vector<uint32_t> device_set;                   // sizes of device-item batches (last gf2x_ctx_prepare)
+    std::unordered_map<uint32_t, uint32_t> child_of;    // split plan slot -> its children's plan slot
+    uint32_t *ws = nullptr;                             // split-plan scratch
+    size_t ws_bytes = 0;
+    cudaEvent_t ws_done = nullptr;                      // recorded after the last split launch
+    cudaStream_t ws_stream = nullptr;
+    bool ws_used = false;
 };
 
 static std::string plan_key(uint32_t n, const gf2x_plan_spec &spec, int checked)
@@ -147,6 +155,10 @@ extern "C" gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
     for (uint32_t S : kLeafSizes)
         if (e == cudaSuccess)
             e = preparer_for(S)(nullptr, 0, 0);
+    if (e == cudaSuccess)
+        e = prepare_split();
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&ctx->ws_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         gf2x_ctx_destroy(ctx);
         return GF2X_ECUDA;
@@ -179,6 +191,10 @@ extern "C" void gf2x_ctx_destroy(gf2x_ctx *ctx)
         cudaFreeHost(ctx->plan_of_n_host);
     if (ctx->plan_of_n_dev)
         cudaFree(ctx->plan_of_n_dev);
+    if (ctx->ws)
+        cudaFree(ctx->ws);
+    if (ctx->ws_done)
+        cudaEventDestroy(ctx->ws_done);
     delete ctx;
 }
 
@@ -192,17 +208,24 @@ static gf2x_status install_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_plan_spec 
         *slot = found->second;
         return GF2X_OK;
     }
-    if (ctx->nplans >= kPlanCapacity)
+    const uint32_t need = spec.split_top ? 2u : 1u;
+    if (ctx->nplans + need > kPlanCapacity)
         return fail(ctx, GF2X_EUNSUPPORTED, "plan table full");
-    GPlan P;
-    gf2x_status st = build_plan(n, &spec, &P, nullptr);
+    GPlan P, C;
+    gf2x_status st = build_plan(n, &spec, &P, nullptr, &C);
     if (st != GF2X_OK)
         return fail(ctx, st, "plan does not fit this size");
     P.checked = checked ? 1u : 0u;
-    const uint32_t s = ctx->nplans++;
+    C.checked = checked ? 1u : 0u;
+    const uint32_t s = ctx->nplans;
+    ctx->nplans += need;
     ctx->plans_host[s] = P;
-    cudaError_t e = cudaMemcpyAsync(ctx->plans_dev + s, ctx->plans_host + s, sizeof(GPlan), cudaMemcpyHostToDevice,
-                                    stream);
+    if (spec.split_top) {
+        ctx->plans_host[s + 1] = C;
+        ctx->child_of[s] = s + 1;
+    }
+    cudaError_t e = cudaMemcpyAsync(ctx->plans_dev + s, ctx->plans_host + s, need * sizeof(GPlan),
+                                    cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "plan upload");
     ctx->slot_of[key] = s;
@@ -396,6 +419,109 @@ static gf2x_status launch(gf2x_ctx *ctx, const LaunchArgs &args, uint32_t S, uns
     return GF2X_OK;
 }
 
+// Scratch of at least `bytes` for split plans (grows only; waits for the
+// device before replacing a smaller buffer).
+static gf2x_status ensure_workspace(gf2x_ctx *ctx, size_t bytes)
+{
+    if (ctx->ws_bytes >= bytes)
+        return GF2X_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "workspace wait");
+    if (ctx->ws)
+        cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    if (cudaMalloc((void **)&ctx->ws, bytes) != cudaSuccess)
+        return fail(ctx, GF2X_ENOMEM, "split workspace allocation");
+    ctx->ws_bytes = bytes;
+    return GF2X_OK;
+}
+
+// The three launches of a split plan over `count` products (strided), in
+// chunks whose scratch fits `ws_bytes` bytes at `ws`.
+static gf2x_status run_split_on(gf2x_ctx *ctx, uint32_t top_slot, uint32_t *ws, size_t ws_bytes, uint64_t *out,
+                                const uint64_t *a, const uint64_t *b, size_t count, size_t stride_in,
+                                size_t stride_out, uint32_t flags, bool persistent, cudaStream_t stream)
+{
+    auto ch = ctx->child_of.find(top_slot);
+    if (ch == ctx->child_of.end())
+        return fail(ctx, GF2X_EINVAL, "split plan without children plan");
+    const GPlan &T = ctx->plans_host[top_slot];
+    const GPlan &C = ctx->plans_host[ch->second];
+    const uint32_t nch = T.lev[0].nch, E = T.lev[0].E;
+    const size_t per = 4ull * nch * 2ull * E;
+    const size_t chunk = std::min<size_t>(count, ws_bytes / per);
+    if (chunk == 0)
+        return fail(ctx, GF2X_EUNSUPPORTED, "scratch too small for one product");
+    const unsigned top_threads = T.threads;
+    const size_t top_smem = 4ull * T.smem_words;
+    for (size_t c0 = 0; c0 < count; c0 += chunk) {
+        const size_t k = std::min(chunk, count - c0);
+        LaunchArgs ta;
+        memset(&ta, 0, sizeof(ta));
+        ta.plans = ctx->plans_dev;
+        ta.base = DevItem{a + c0 * stride_in, b + c0 * stride_in, out + c0 * stride_out, top_slot, flags};
+        ta.stride_in = stride_in;
+        ta.stride_out = stride_out;
+        ta.count = (uint32_t)k;
+        ta.mode = kItemsStrided;
+        ta.err = ctx->err_dev;
+        ta.persistent = persistent ? 1u : 0u;
+        const unsigned tgrid = (unsigned)(persistent ? std::min<size_t>(k, 4ull * ctx->sm_count) : k);
+        cudaError_t e = launch_split_eval(ta, ws, tgrid, top_threads, top_smem, stream);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "split evaluation launch");
+        // children: independent full products of E words, written over their operand slots
+        LaunchArgs ca;
+        memset(&ca, 0, sizeof(ca));
+        ca.plans = ctx->plans_dev;
+        ca.base = DevItem{reinterpret_cast<const uint64_t *>(ws), reinterpret_cast<const uint64_t *>(ws + E),
+                          reinterpret_cast<uint64_t *>(ws), ch->second, 0u};
+        ca.stride_in = E;    // 2E words = E limbs per slot
+        ca.stride_out = E;
+        ca.count = (uint32_t)(k * nch);
+        ca.mode = kItemsStrided;
+        ca.err = ctx->err_dev;
+        gf2x_status st = launch(ctx, ca, C.S, C.threads, 4ull * C.smem_words, k * nch, persistent, stream);
+        if (st != GF2X_OK)
+            return st;
+        e = launch_split_interp(ta, ws, tgrid, top_threads, top_smem, stream);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "split interpolation launch");
+    }
+    return GF2X_OK;
+}
+
+static gf2x_status run_split(gf2x_ctx *ctx, uint32_t top_slot, uint64_t *out, const uint64_t *a, const uint64_t *b,
+                             size_t count, size_t stride_in, size_t stride_out, uint32_t flags, bool persistent,
+                             cudaStream_t stream)
+{
+    const GPlan &T = ctx->plans_host[top_slot];
+    const size_t per = 4ull * T.lev[0].nch * 2ull * T.lev[0].E;
+    const size_t want = std::max<size_t>(per, std::min<size_t>(count * per, kWorkspaceCap / per * per));
+    gf2x_status st = ensure_workspace(ctx, want);
+    if (st != GF2X_OK)
+        return st;
+    // the scratch is shared by every split call of the context: order this
+    // call after the previous one when it came on another stream
+    if (ctx->ws_used && ctx->ws_stream != stream) {
+        cudaError_t e = cudaStreamWaitEvent(stream, ctx->ws_done, 0);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "workspace ordering");
+    }
+    st = run_split_on(ctx, top_slot, ctx->ws, ctx->ws_bytes, out, a, b, count, stride_in, stride_out, flags,
+                      persistent, stream);
+    if (st != GF2X_OK)
+        return st;
+    cudaError_t e = cudaEventRecord(ctx->ws_done, stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "workspace event");
+    ctx->ws_used = true;
+    ctx->ws_stream = stream;
+    return GF2X_OK;
+}
+
 static gf2x_status one_product(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n,
                                uint32_t flags, gf2x_stream stream)
 {
@@ -412,6 +538,8 @@ static gf2x_status one_product(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, 
     if (st != GF2X_OK)
         return st;
     const GPlan &P = ctx->plans_host[slot];
+    if (P.split)
+        return run_split(ctx, slot, out, a, b, 1, 0, 0, flags, false, s);
     LaunchArgs args;
     memset(&args, 0, sizeof(args));
     args.plans = ctx->plans_dev;
@@ -455,6 +583,9 @@ extern "C" gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint
     if (st != GF2X_OK)
         return st;
     const GPlan &P = ctx->plans_host[slot];
+    if (P.split)
+        return run_split(ctx, slot, out, a, b, count, stride_in, stride_out, flags,
+                         (batch_flags & GF2X_BATCH_PERSISTENT) != 0, s);
     LaunchArgs args;
     memset(&args, 0, sizeof(args));
     args.plans = ctx->plans_dev;
@@ -531,6 +662,8 @@ extern "C" gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, s
             if (st != GF2X_OK)
                 return st;
             const GPlan &P = ctx->plans_host[slot];
+            if (P.split)
+                return fail(ctx, GF2X_EUNSUPPORTED, "split plans run through gf2x_mul_strided / gf2x_mul only");
             if (S && P.S != S)
                 return fail(ctx, GF2X_EUNSUPPORTED, "device item batches need one leaf size over the prepared plans");
             S = P.S;
@@ -565,6 +698,8 @@ extern "C" gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, s
         st = plan_for(ctx, it.n, s, &slot);
         if (st != GF2X_OK)
             return st;
+        if (ctx->plans_host[slot].split)
+            return fail(ctx, GF2X_EUNSUPPORTED, "split plans run through gf2x_mul_strided / gf2x_mul only");
         dv[i] = DevItem{it.a, it.b, it.out, slot, it.flags};
         Ss[i] = ctx->plans_host[slot].S;
     }
@@ -688,7 +823,8 @@ extern "C" gf2x_status gf2x_ctx_launch_shape(gf2x_ctx *ctx, uint32_t n, uint32_t
     gf2x_status st = plan_for(ctx, n, nullptr, &slot);
     if (st != GF2X_OK)
         return st;
-    const GPlan &P = ctx->plans_host[slot];
+    auto chs = ctx->child_of.find(slot);
+    const GPlan &P = ctx->plans_host[chs != ctx->child_of.end() ? chs->second : slot];
     int per_sm = 0;
     cudaError_t e = preparer_for(P.S)(&per_sm, P.threads, 4ull * P.smem_words);
     if (e != cudaSuccess)

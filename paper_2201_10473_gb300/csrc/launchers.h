@@ -16,6 +16,12 @@ GF2X_DECLARE_LEAF(12)
 GF2X_DECLARE_LEAF(16)
 #undef GF2X_DECLARE_LEAF
 
+cudaError_t launch_split_eval(const LaunchArgs &a, uint32_t *scratch, unsigned grid, unsigned block, size_t smem,
+                              cudaStream_t st);
+cudaError_t launch_split_interp(const LaunchArgs &a, const uint32_t *scratch, unsigned grid, unsigned block,
+                                size_t smem, cudaStream_t st);
+cudaError_t prepare_split();
+
 typedef cudaError_t (*LaunchFn)(const LaunchArgs &, unsigned, unsigned, size_t, cudaStream_t);
 typedef cudaError_t (*PrepareFn)(int *, unsigned, size_t);
 

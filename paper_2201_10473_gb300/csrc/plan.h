@@ -65,7 +65,7 @@ struct GPlan {
     uint32_t part_words;
     uint32_t checked;    // verify exactness invariants on the device
     uint32_t fuse_k2;    // 1: the last level is a 2-way Karatsuba done inside the leaf thread
-    uint32_t reserved;
+    uint32_t split;      // 1: this is the top level of a split plan (children go through global scratch)
     uint32_t pad2_;
     GLevel lev[kMaxLevels];
 };

@@ -84,7 +84,9 @@ static gf2x_status check_spec_shape(const gf2x_plan_spec &s)
         return GF2X_EINVAL;
     if (s.threads && (s.threads % 32 || s.threads > 1024))
         return GF2X_EINVAL;
-    if (s.fuse_leaf > 1)
+    if (s.fuse_leaf > 1 || s.split_top > 1)
+        return GF2X_EINVAL;
+    if (s.split_top && s.nlev < 2)
         return GF2X_EINVAL;
     if (s.fuse_leaf) {
         if (s.nlev < 1 || s.kind[s.nlev - 1] != GF2X_LEVEL_KARATSUBA || s.arg[s.nlev - 1] != 2)
@@ -98,14 +100,16 @@ static gf2x_status check_spec_shape(const gf2x_plan_spec &s)
 static void fill_karatsuba_tables(GLevel &L)
 {
     const uint32_t k = L.k;
+    if (k < 2 || k > 5)   // validated by check_spec_shape; bounds the tables below
+        return;
     uint32_t j = 0;
-    for (uint32_t i = 0; i < k; ++i, ++j) {
+    for (uint32_t i = 0; i < k && j < 16; ++i, ++j) {
         L.sel[j][0] = (uint8_t)i;
         L.sel[j][1] = 255;
     }
     uint32_t pairidx[5][5];
     for (uint32_t i = 0; i < k; ++i)
-        for (uint32_t i2 = i + 1; i2 < k; ++i2, ++j) {
+        for (uint32_t i2 = i + 1; i2 < k && j < 16; ++i2, ++j) {
             L.sel[j][0] = (uint8_t)i;
             L.sel[j][1] = (uint8_t)i2;
             pairidx[i][i2] = j;
@@ -113,11 +117,11 @@ static void fill_karatsuba_tables(GLevel &L)
     for (uint32_t p = 0; p + 1 < 2 * k; ++p) {
         uint32_t c = 0;
         for (uint32_t i = 0; i < k; ++i)
-            if (p >= i && p - i < k)
+            if (p >= i && p - i < k && c < (uint32_t)kMaxTerms)
                 L.terms[p][c++] = (uint8_t)i;
         for (uint32_t i = 0; i < k; ++i) {
             uint32_t i2 = p - i;
-            if (p >= i && i < i2 && i2 < k)
+            if (p >= i && i < i2 && i2 < k && c < (uint32_t)kMaxTerms)
                 L.terms[p][c++] = (uint8_t)pairidx[i][i2];
         }
         L.nterms[p] = (uint8_t)c;
@@ -155,7 +159,11 @@ static void op_model(const GPlan &P, const uint32_t *sz, const uint32_t *npar_al
     (void)sz;
 }
 
-gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec_in, GPlan *out, gf2x_plan_info *info)
+static gf2x_status build_split_plan(uint32_t n, const gf2x_plan_spec &s, GPlan *out, gf2x_plan_info *info,
+                                    GPlan *child_out);
+
+gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec_in, GPlan *out, gf2x_plan_info *info,
+                       GPlan *child_out)
 {
     if (!spec_in)
         return GF2X_EINVAL;
@@ -165,6 +173,9 @@ gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec_in, GPlan *out, gf
     gf2x_status st = check_spec_shape(s);
     if (st != GF2X_OK)
         return st;
+
+    if (s.split_top)
+        return build_split_plan(n, s, out, info, child_out);
 
     const uint32_t L32 = (n + 31) / 32;
     uint32_t sz[kMaxLevels + 1];
@@ -343,6 +354,151 @@ gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec_in, GPlan *out, gf
         info->bytes_in = 2ull * 8 * P.L64;
         info->bytes_out_full = 8ull * P.Lfull64;
         info->bytes_out_reduced = 8ull * P.L64;
+        info->scratch_bytes = 0;
+    }
+    return GF2X_OK;
+}
+
+// Split plan: level 0 across CTAs.  The children are products of E0 words
+// (n_child = 32 E0 bits, full products of 2 E0 words written over their
+// operand slot in scratch); the top plan holds level 0 alone with its own
+// shared-memory layout (operands / product, children, Toom temporaries).
+static gf2x_status build_split_plan(uint32_t n, const gf2x_plan_spec &s, GPlan *out, gf2x_plan_info *info,
+                                    GPlan *child_out)
+{
+    if (out && !child_out)
+        return GF2X_EINVAL;
+    gf2x_plan_spec cs;
+    memset(&cs, 0, sizeof(cs));
+    cs.nlev = s.nlev - 1;
+    for (uint32_t l = 1; l < s.nlev; ++l) {
+        cs.kind[l - 1] = s.kind[l];
+        cs.arg[l - 1] = s.arg[l];
+    }
+    cs.leaf_words = s.leaf_words;
+    cs.threads = s.threads;
+    cs.seq_top = s.seq_top;
+    cs.fuse_leaf = s.fuse_leaf;
+    if (cs.seq_top && cs.nlev < 2)
+        return GF2X_EINVAL;
+    // the child size: smallest leaf such that the full tree covers n
+    const uint32_t L32 = (n + 31) / 32;
+    uint32_t sz[kMaxLevels + 1];
+    uint32_t S = s.leaf_words;
+    gf2x_plan_spec probe = s;
+    probe.split_top = 0;
+    if (S == 0) {
+        for (uint32_t cand : kLeafSizes) {
+            if (s.fuse_leaf && cand > kMaxFusedLeaf)
+                continue;
+            if (level_sizes(probe, cand, sz) && sz[0] >= L32) {
+                S = cand;
+                break;
+            }
+        }
+        if (S == 0)
+            return GF2X_EUNSUPPORTED;
+    }
+    if (!level_sizes(probe, S, sz))
+        return GF2X_EINVAL;
+    if (sz[0] < L32)
+        return GF2X_EUNSUPPORTED;
+    const uint32_t T0 = sz[0], E0 = sz[1];
+    if (E0 & 1u)
+        return GF2X_EINVAL;
+    cs.leaf_words = S;
+    if (32ull * E0 > GF2X_MAX_N)
+        return GF2X_EUNSUPPORTED;
+    GPlan C;
+    gf2x_plan_info ci;
+    gf2x_status st = build_plan(32u * E0, &cs, &C, &ci);
+    if (st != GF2X_OK)
+        return st;
+
+    GPlan P;
+    memset(&P, 0, sizeof(P));
+    P.n = n;
+    P.L32 = L32;
+    P.L64 = (n + 63) / 64;
+    P.Lfull64 = (uint32_t)((2ull * n - 1 + 63) / 64);
+    P.T0 = T0;
+    P.nlev = 1;
+    P.S = C.S;
+    P.split = 1;
+    P.threads = 256;
+    GLevel &L = P.lev[0];
+    L.kind = s.kind[0] == GF2X_LEVEL_KARATSUBA ? kKaratsuba : kToom3;
+    L.T = T0;
+    L.E = E0;
+    if (L.kind == kKaratsuba) {
+        L.k = s.arg[0];
+        L.W = 0;
+        L.np = E0;
+        L.nch = L.k * (L.k + 1) / 2;
+        fill_karatsuba_tables(L);
+    } else {
+        L.k = 3;
+        L.W = s.arg[0];
+        L.np = E0 - 2 * L.W;
+        L.nch = 5;
+    }
+    L.npar = 1;
+    L.div2E = make_div(2 * E0);
+    L.divnch = make_div(L.nch);
+    L.divE = make_div(E0);
+    L.div2T = make_div(2 * T0);
+    L.divhE = make_div(std::max(1u, E0 / 2));
+    uint32_t off = 0;
+    P.top_off = off;
+    L.in_off = off;
+    off += round_up(2 * T0, 4);
+    L.ch_off = off;
+    off += round_up(L.nch * 2 * E0, 4);
+    P.tmp_off = off;
+    if (L.kind == kToom3)
+        off += round_up(4 * E0, 4);
+    P.part_off = off;
+    P.part_words = round_up(std::max(P.threads, L.W), 4);
+    off += P.part_words;
+    P.smem_words = off;
+    if (4ull * off > kMaxDynamicSmemBytes)
+        return GF2X_EUNSUPPORTED;
+    const uint64_t xe = (uint64_t)L.nch * 2 * E0, xi = 2ull * T0;
+    if (xe * (2ull * E0) >= (1ull << 32) || xi * xi >= (1ull << 32) || xi * E0 >= (1ull << 32))
+        return GF2X_EUNSUPPORTED;
+
+    if (out) {
+        *out = P;
+        *child_out = C;
+    }
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->n = n;
+        info->top_words = T0;
+        info->leaf_words = C.S;
+        info->nleaves = L.nch * ci.nleaves;
+        info->threads = C.threads;
+        info->smem_bytes = (uint32_t)std::max<uint64_t>(4ull * off, ci.smem_bytes);
+        info->level_words[0] = T0;
+        for (uint32_t d = 0; d < cs.nlev + 1 && d + 1 <= (uint32_t)kMaxLevels; ++d)
+            info->level_words[d + 1] = ci.level_words[d];
+        // top level work (same model as an in-CTA level) plus the children's
+        uint64_t top = 0;
+        if (L.kind == kKaratsuba) {
+            uint64_t pairs = (uint64_t)L.k * (L.k - 1) / 2, terms = 0;
+            for (uint32_t q = 0; q + 1 < 2 * L.k; ++q)
+                terms += L.nterms[q];
+            top = pairs * 2ull * E0 + terms * 2ull * E0 - 2ull * T0;
+        } else {
+            top = 2ull * (2ull * L.np + 4ull * E0) + 36ull * L.np;
+        }
+        info->ops_leaf = (uint64_t)L.nch * ci.ops_leaf;
+        info->ops_full = top + (uint64_t)L.nch * (ci.ops_full - 4ull * (32u * E0 / 64)) + 4ull * P.L64;
+        info->clmul64 = (uint64_t)L.nch * ci.clmul64;
+        info->bytes_in = 2ull * 8 * P.L64;
+        info->bytes_out_full = 8ull * P.Lfull64;
+        info->bytes_out_reduced = 8ull * P.L64;
+        info->scratch_bytes = 4ull * L.nch * 2 * E0;
     }
     return GF2X_OK;
 }
@@ -426,6 +582,55 @@ gf2x_status default_spec(uint32_t n, gf2x_plan_spec *out)
             }
         }
     }
+    // no plan fits one CTA: split the top level across CTAs
+    {
+        bool found = false;
+        uint64_t best_ops = ~0ull;
+        gf2x_plan_spec best;
+        for (uint32_t W : toomW) {
+            for (const auto &ks : kseqs) {
+                gf2x_plan_spec sp;
+                memset(&sp, 0, sizeof(sp));
+                uint32_t l = 0;
+                if (W) {
+                    sp.kind[l] = GF2X_LEVEL_TOOM3;
+                    sp.arg[l++] = W;
+                }
+                for (uint32_t k : ks) {
+                    if (l >= (uint32_t)kMaxLevels)
+                        break;
+                    sp.kind[l] = GF2X_LEVEL_KARATSUBA;
+                    sp.arg[l++] = k;
+                }
+                sp.nlev = l;
+                sp.split_top = 1;
+                if (l < 2)
+                    continue;
+                for (uint32_t seq = 0; seq <= 1; ++seq) {
+                    sp.seq_top = seq;
+                    if (seq && l < 3)
+                        continue;
+                    for (uint32_t S : kLeafSizes) {
+                        sp.leaf_words = S;
+                        sp.fuse_leaf = (sp.kind[l - 1] == GF2X_LEVEL_KARATSUBA && sp.arg[l - 1] == 2 &&
+                                        S <= kMaxFusedLeaf) ? 1u : 0u;
+                        gf2x_plan_info info;
+                        if (build_plan(n, &sp, nullptr, &info) != GF2X_OK)
+                            continue;
+                        if (info.ops_full < best_ops) {
+                            best_ops = info.ops_full;
+                            best = sp;
+                            found = true;
+                        }
+                    }
+                }
+            }
+        }
+        if (found) {
+            *out = best;
+            return GF2X_OK;
+        }
+    }
     return GF2X_EUNSUPPORTED;
 }
 
@@ -445,7 +650,7 @@ gf2x_status parse_spec(const char *text, gf2x_plan_spec *out)
             break;
         pos = q + 1;
     }
-    if (fields.size() > 5)
+    if (fields.size() > 6)
         return GF2X_EINVAL;
     // levels
     const std::string &lv = fields[0];
@@ -473,7 +678,7 @@ gf2x_status parse_spec(const char *text, gf2x_plan_spec *out)
             break;
         i = j + 1;
     }
-    uint32_t *dst[4] = {&s.leaf_words, &s.threads, &s.seq_top, &s.fuse_leaf};
+    uint32_t *dst[5] = {&s.leaf_words, &s.threads, &s.seq_top, &s.fuse_leaf, &s.split_top};
     for (size_t f = 1; f < fields.size(); ++f) {
         if (fields[f].empty())
             continue;

@@ -15,7 +15,10 @@ constexpr uint64_t kMaxDynamicSmemBytes = 232448ull - sizeof(GPlan) - 256;
 
 uint32_t max_threads_for_leaf(uint32_t S);
 bool leaf_supported(uint32_t S);
-gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec, GPlan *out, gf2x_plan_info *info);
+// For a split plan (spec->split_top) `out` receives the top-level plan and
+// `child_out` the plan of the children (which must then be non-null).
+gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec, GPlan *out, gf2x_plan_info *info,
+                       GPlan *child_out = nullptr);
 gf2x_status default_spec(uint32_t n, gf2x_plan_spec *out);
 gf2x_status parse_spec(const char *text, gf2x_plan_spec *out);
 

@@ -40,7 +40,8 @@ class Gf2xError(RuntimeError):
 class PlanSpec(ctypes.Structure):
     _fields_ = [("nlev", ctypes.c_uint32), ("kind", ctypes.c_uint32 * MAX_LEVELS),
                 ("arg", ctypes.c_uint32 * MAX_LEVELS), ("leaf_words", ctypes.c_uint32),
-                ("threads", ctypes.c_uint32), ("seq_top", ctypes.c_uint32), ("fuse_leaf", ctypes.c_uint32)]
+                ("threads", ctypes.c_uint32), ("seq_top", ctypes.c_uint32), ("fuse_leaf", ctypes.c_uint32),
+                ("split_top", ctypes.c_uint32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -48,7 +49,8 @@ class PlanInfo(ctypes.Structure):
                 ("nleaves", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("smem_bytes", ctypes.c_uint32),
                 ("level_words", ctypes.c_uint32 * (MAX_LEVELS + 1)), ("ops_full", ctypes.c_uint64),
                 ("ops_leaf", ctypes.c_uint64), ("clmul64", ctypes.c_uint64), ("bytes_in", ctypes.c_uint64),
-                ("bytes_out_full", ctypes.c_uint64), ("bytes_out_reduced", ctypes.c_uint64)]
+                ("bytes_out_full", ctypes.c_uint64), ("bytes_out_reduced", ctypes.c_uint64),
+                ("scratch_bytes", ctypes.c_uint64)]
 
 
 class Item(ctypes.Structure):
@@ -126,7 +128,7 @@ def parse_spec(text: str) -> PlanSpec:
 
 def spec_text(s: PlanSpec) -> str:
     lv = ".".join(("K" if s.kind[i] == LEVEL_KARATSUBA else "T") + str(s.arg[i]) for i in range(s.nlev))
-    return f"{lv}/{s.leaf_words}/{s.threads}/{s.seq_top}/{s.fuse_leaf}"
+    return f"{lv}/{s.leaf_words}/{s.threads}/{s.seq_top}/{s.fuse_leaf}/{s.split_top}"
 
 
 def default_spec(n: int) -> str:

@@ -88,7 +88,7 @@ def test_paper_sizes_through_the_abi():
     assert checked >= 13
 
 
-@pytest.mark.parametrize("n", CONFIG_SIZES + [1, 2, 63, 64, 65, 1000, 4096, 65536])
+@pytest.mark.parametrize("n", CONFIG_SIZES + [1, 2, 63, 64, 65, 1000, 4096, 65536, 100000, 120001, 131072])
 def test_default_plan_covers_n_and_fits(n):
     spec = gf2x.default_spec(n)
     info = gf2x.plan_info(n, spec)
@@ -111,11 +111,11 @@ def test_clmul_counts_table_compkarat_through_abi():
 
 
 def test_spec_parse_roundtrip_and_errors():
-    s = gf2x.parse_spec("T2.K3.K2.K2/8/288/0/1")
-    assert gf2x.spec_text(s) == "T2.K3.K2.K2/8/288/0/1"
-    assert gf2x.spec_text(gf2x.parse_spec("K3")) == "K3/0/0/0/0"
+    s = gf2x.parse_spec("T2.K3.K2.K2/8/288/0/1/1")
+    assert gf2x.spec_text(s) == "T2.K3.K2.K2/8/288/0/1/1"
+    assert gf2x.spec_text(gf2x.parse_spec("K3")) == "K3/0/0/0/0/0"
     for bad in ["K4/8", "X2", "T0", "K2/7", "K2/8/100", "K2/8/0/1", "K2/8/0/0/9", "K3/8/0/0/1", "K2/12/0/0/1",
-                "K2/8/0/0/0/0"]:
+                "K2/8/0/0/0/2", "K2/8/0/0/0/1", "K2/8/0/0/0/0/0"]:
         with pytest.raises(gf2x.Gf2xError):
             gf2x.parse_spec(bad)
 
@@ -147,3 +147,16 @@ def test_paper_hqc_plans_through_the_abi():
     assert 32 * a["top_words"] == 18048 and a["nleaves"] == 5 * 6 * 27
     b = gf2x.plan_info(57637, "T16.K5.K2.K2.K2.K2/8/0/1")
     assert 32 * b["top_words"] == 58368 and b["nleaves"] == 5 * 15 * 81
+
+
+def test_split_plan_facts():
+    """Split plans: the top level's children are products of E0 words; the
+    size rule is the same; scratch is nch x 2E0 words per product."""
+    info = gf2x.plan_info(57637, "T16.K5.K2.K2.K2.K2/8/0/0/1/1")
+    assert 32 * info["top_words"] == 58368
+    assert info["level_words"][:2] == [1824, 640]
+    assert info["scratch_bytes"] == 4 * 5 * 2 * 640
+    assert info["nleaves"] == 5 * 15 * 81          # leaf products (the fused level counted at its leaves)
+    whole = gf2x.plan_info(57637, "T16.K5.K2.K2.K2.K2/8/0/1/1/0")
+    assert whole["nleaves"] == info["nleaves"]
+    assert gf2x.plan_info(131072, None)["scratch_bytes"] > 0      # only split plans reach the maximum size

@@ -336,3 +336,44 @@ def test_replayed_graph_refuses_a_plan_changed_under_it():
         assert int(o.abs().sum()) == 0               # nothing was written
     finally:
         c2.close()
+
+
+# ------------------------------------------------------------ split plans (top level across CTAs)
+
+SPLIT_PLANS = [
+    (17669, "T2.K2.K2.K2.K2.K2/6/128/1/0/1"), (17669, "K3.K2.K2.K2.K2.K2/6/0/0/1/1"),
+    (57637, "T16.K5.K2.K2.K2.K2/8/0/0/1/1"), (57637, "T16.K2.K2.K2.K2.K2.K2/10/448/1/1/1"),
+    (57637, "K5.K2.K2.K2.K2.K2/12/0/1/0/1"), (35851, "T4.K2.K2.K2.K2.K2.K2/6/0/1/1/1"),
+    (100000, None), (131072, None), (120001, None),
+]
+
+
+@pytest.mark.parametrize("n,spec", SPLIT_PLANS)
+def test_split_plans(ctx, n, spec):
+    """The top level evaluated/interpolated by its own kernels through global
+    scratch, the children as independent products: bit-exact, batched and single."""
+    if spec is not None:
+        ctx.set_plan(n, spec)
+    try:
+        sp = ctx.get_plan(n)
+        a, b = wl.dense_pair(7000 + n, n, 5)
+        check_batch(ctx, a, b, n, True)
+        check_batch(ctx, a, b, n, False)
+        check_batch(ctx, a, b, n, True, persistent=True)
+        da, db = to_dev(a[0]), to_dev(b[0])
+        assert np.array_equal(to_host(ctx.mulmod(da, db, n)), oracle.mulmod(a[0], b[0], n)), sp
+        ctx.sync_status()
+    finally:
+        if spec is not None:
+            ctx.set_plan(n, None)
+
+
+def test_split_plan_in_checked_mode_and_large_batch_chunks(ctx):
+    n = 131072
+    ctx.set_checked(True)
+    try:
+        a, b = wl.dense_pair(7100, n, 3)
+        check_batch(ctx, a, b, n, True)
+        ctx.sync_status()
+    finally:
+        ctx.set_checked(False)
