@@ -233,6 +233,38 @@ gf2x_status gf2x_ctx_sync_status(gf2x_ctx *ctx, gf2x_stream stream);
  * call on it). */
 const char *gf2x_ctx_last_error(gf2x_ctx *ctx);
 
+/* ---- Products with no allocation at all ----------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory: code that runs while a CUDA stream
+ * is being captured into a graph (cudaMalloc is not allowed there), code
+ * under a fixed memory budget or a no-allocation-after-start-up rule, and
+ * hosts that hand the library device buffers but no allocator.
+ *
+ * gf2x_mul_strided_static computes the same `count` products as
+ * gf2x_mul_strided (same operand/result layout, strides in limbs, flags
+ * GF2X_REDUCE or 0), with a split plan (spec->split_top = 1; spec = NULL
+ * picks the split plan with the fewest modelled operations for n), and needs
+ * no context.  Its scratch is a file-scope device array of
+ * GF2X_STATIC_SCRATCH_BYTES that every GPU which loads the library holds
+ * until the process exits; its two plans live in a second such array.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *  - Set-up: the first call on a device (with that device current) looks up
+ *    the arrays' device addresses and sets the kernels' shared-memory limits;
+ *    make that first call before any stream capture.
+ *  - Limit: count x gf2x_plan_info.scratch_bytes of the plan must not exceed
+ *    GF2X_STATIC_SCRATCH_BYTES, else GF2X_EUNSUPPORTED (split the batch).
+ *  - Sharing: every call uses the same arrays, which keep the last call's
+ *    contents (nothing in them needs to start at zero); calls whose work
+ *    overlaps on the GPU (other streams, other host threads) race — order
+ *    them on one stream.
+ *  - Errors: GF2X_EINVAL for bad pointers, overlap, flags or a spec that is
+ *    not a split plan; launch failures as GF2X_ECUDA. */
+#define GF2X_STATIC_SCRATCH_BYTES (4u << 20)
+
+gf2x_status gf2x_mul_strided_static(uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n, size_t count,
+                                    size_t stride_in, size_t stride_out, uint32_t flags,
+                                    const gf2x_plan_spec *spec, gf2x_stream stream);
+
 /* ---- Plan cost model network (the autotuner's learned part) -------------
  * A two-layer perceptron y = w2 . relu(W1 x + b1) + b2 in fp32 that predicts
  * the log time of a recursion plan from its descriptor.  The paper has no

@@ -634,6 +634,59 @@ gf2x_status default_spec(uint32_t n, gf2x_plan_spec *out)
     return GF2X_EUNSUPPORTED;
 }
 
+gf2x_status default_split_spec(uint32_t n, gf2x_plan_spec *out)
+{
+    if (!out)
+        return GF2X_EINVAL;
+    if (n < 1 || n > GF2X_MAX_N)
+        return GF2X_EUNSUPPORTED;
+    std::vector<std::vector<uint32_t>> kseqs;
+    std::vector<uint32_t> cur;
+    enumerate_kseq(kseqs, cur, 5, 6);
+    const uint32_t toomW[] = {0, 1, 2, 4, 8, 16};
+    bool found = false;
+    uint64_t best_ops = ~0ull;
+    gf2x_plan_spec best;
+    for (uint32_t W : toomW) {
+        for (const auto &ks : kseqs) {
+            gf2x_plan_spec sp;
+            memset(&sp, 0, sizeof(sp));
+            uint32_t l = 0;
+            if (W) {
+                sp.kind[l] = GF2X_LEVEL_TOOM3;
+                sp.arg[l++] = W;
+            }
+            for (uint32_t k : ks) {
+                if (l >= (uint32_t)kMaxLevels)
+                    break;
+                sp.kind[l] = GF2X_LEVEL_KARATSUBA;
+                sp.arg[l++] = k;
+            }
+            sp.nlev = l;
+            sp.split_top = 1;
+            if (l < 2)
+                continue;
+            for (uint32_t S : kLeafSizes) {
+                sp.leaf_words = S;
+                sp.fuse_leaf = (sp.kind[l - 1] == GF2X_LEVEL_KARATSUBA && sp.arg[l - 1] == 2 && S <= kMaxFusedLeaf)
+                                   ? 1u : 0u;
+                gf2x_plan_info info;
+                if (build_plan(n, &sp, nullptr, &info) != GF2X_OK)
+                    continue;
+                if (info.ops_full < best_ops) {
+                    best_ops = info.ops_full;
+                    best = sp;
+                    found = true;
+                }
+            }
+        }
+    }
+    if (!found)
+        return GF2X_EUNSUPPORTED;
+    *out = best;
+    return GF2X_OK;
+}
+
 gf2x_status parse_spec(const char *text, gf2x_plan_spec *out)
 {
     if (!text || !out)

@@ -21,5 +21,7 @@ gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec, GPlan *out, gf2x_
                        GPlan *child_out = nullptr);
 gf2x_status default_spec(uint32_t n, gf2x_plan_spec *out);
 gf2x_status parse_spec(const char *text, gf2x_plan_spec *out);
+// The split plan (split_top = 1) with the fewest modelled operations for n.
+gf2x_status default_split_spec(uint32_t n, gf2x_plan_spec *out);
 
 }  // namespace gf2x
