@@ -207,6 +207,16 @@ def config_of(w, spec, shape):
 
 # ---------------------------------------------------------------- our arm
 
+def launches_per_step(info: dict, batch: int) -> int:
+    """Kernel launches of one batched call: 1, or 3 per scratch chunk for a
+    split plan (evaluation, children, interpolation)."""
+    per = info.get("scratch_bytes", 0)
+    if not per:
+        return 1
+    chunk = max(1, min(batch, (256 << 20) // per))
+    return 3 * (-(-batch // chunk))
+
+
 def kernel_source_hash() -> str:
     """Hash of the fused kernel's source: traffic counters apply only to this version."""
     import hashlib
@@ -407,7 +417,7 @@ def run_ours(args, w):
         "config": config_of(w, spec, shape),
         "e2e": {"value": e2e_value, "unit": "mults/s", "h2d_bytes_per_step": int(pin_a.numel() * 8 * 2),
                 "d2h_bytes_per_step": int(pin_out.numel() * 8), "steps": K2},
-        "gpu_launches": K,
+        "gpu_launches": K * launches_per_step(info, batch),
         "roofline": roof,
         "cpu_baseline": cpu,
         "plain": plain,

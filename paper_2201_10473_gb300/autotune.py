@@ -41,8 +41,10 @@ def _kseqs(max_depth: int = 7):
     return out
 
 
-def candidate_specs(n: int, max_waste: float = 1.30, threads=THREAD_CHOICES, limit: int | None = None):
-    """Valid plan specs for size n whose padded size is at most max_waste * n."""
+def candidate_specs(n: int, max_waste: float = 1.30, threads=THREAD_CHOICES, limit: int | None = None,
+                    split_from: int = 24000):
+    """Valid plan specs for size n whose padded size is at most max_waste * n
+    (split-top plans too, for n >= split_from)."""
     seen = set()
     out = []
     for W in TOOM_SHIFTS:
@@ -52,9 +54,8 @@ def candidate_specs(n: int, max_waste: float = 1.30, threads=THREAD_CHOICES, lim
                 continue
             base = ".".join(levels)
             for S in (4, 6, 8, 10, 12, 16):
-                for seq in (0, 1):
-                    for fuse in (0, 1):
-                        spec0 = f"{base}/{S}/0/{seq}/{fuse}"
+                for seq, fuse, split in itertools.product((0, 1), (0, 1), (0, 1) if n >= split_from else (0,)):
+                        spec0 = f"{base}/{S}/0/{seq}/{fuse}/{split}"
                         try:
                             info = gf2x.plan_info(n, spec0)
                         except gf2x.Gf2xError:
@@ -65,13 +66,13 @@ def candidate_specs(n: int, max_waste: float = 1.30, threads=THREAD_CHOICES, lim
                         for t in threads:
                             if t and (t > maxT or t < 64):
                                 continue
-                            spec = f"{base}/{S}/{t}/{seq}/{fuse}"
+                            spec = f"{base}/{S}/{t}/{seq}/{fuse}/{split}"
                             if t:
                                 try:
                                     gf2x.plan_info(n, spec)
                                 except gf2x.Gf2xError:
                                     continue
-                            key = (base, S, t or info["threads"], seq, fuse)
+                            key = (base, S, t or info["threads"], seq, fuse, split)
                             if key in seen:
                                 continue
                             seen.add(key)
@@ -199,6 +200,9 @@ def mixed_plan_sets(records: list, weights: dict, batch: int, top: int = 3) -> l
     for r in records:
         if r["n"] not in weights or abs(math.log2(r["batch"]) - math.log2(batch)) > 1.0:
             continue
+        fields = r["spec"].split("/")
+        if len(fields) > 5 and fields[5] == "1":
+            continue    # split plans run through strided launches only
         S = int(r["spec"].split("/")[1])
         key = (r["n"], S, r["threads"])
         ns = r["ms"] * 1e6 / r["batch"]
