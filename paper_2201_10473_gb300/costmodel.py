@@ -16,7 +16,7 @@ import numpy as np
 
 from . import gf2x
 
-IN_DIM = 16
+IN_DIM = 17
 HIDDEN = 64
 
 _MLP_SIGS = {
@@ -83,6 +83,7 @@ def plan_features(n: int, batch: int, spec: str) -> np.ndarray:
     f[13] = math.log2(info["ops_full"]) / 30
     f[14] = math.log2(max(1, info["nleaves"])) / 14
     f[15] = info["smem_bytes"] / 232448
+    f[16] = s.split_top
     return f
 
 
