@@ -195,11 +195,13 @@ gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, co
  *  - Host `items`: every item is checked, its plan resolved, and the array
  *    copied through a pinned staging buffer of the context (a ring of four;
  *    a reused buffer is first waited for on the host).  Items whose plans
- *    share a leaf size run in one launch (one launch per leaf size).
+ *    share a leaf size run in one launch (one launch per leaf size); items
+ *    with a split plan run as that plan's three launches per plan.
  *  - GF2X_BATCH_ITEMS_ON_DEVICE: `items` is a device array of gf2x_item read
  *    by the kernel, which looks each plan up by n on the device among the
  *    sizes of the last gf2x_ctx_prepare call; those plans must share one
- *    leaf size (else GF2X_EUNSUPPORTED).  The launch gets the largest CTA and
+ *    leaf size and none may be a split plan (else GF2X_EUNSUPPORTED).  The
+ *    launch gets the largest CTA and
  *    shared memory of those plans; a plan that does not match the launch is
  *    refused on the device and reported (never run).  An item whose n has no
  *    plan is skipped and reported by gf2x_ctx_sync_status; an item with

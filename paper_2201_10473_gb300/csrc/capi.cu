@@ -438,11 +438,12 @@ static gf2x_status ensure_workspace(gf2x_ctx *ctx, size_t bytes)
     return GF2X_OK;
 }
 
-// The three launches of a split plan over `count` products (strided), in
-// chunks whose scratch fits `ws_bytes` bytes at `ws`.
-static gf2x_status run_split_on(gf2x_ctx *ctx, uint32_t top_slot, uint32_t *ws, size_t ws_bytes, uint64_t *out,
-                                const uint64_t *a, const uint64_t *b, size_t count, size_t stride_in,
-                                size_t stride_out, uint32_t flags, bool persistent, cudaStream_t stream)
+// The three launches of a split plan over `count` products, in chunks whose
+// scratch fits `ws_bytes` bytes at `ws`.  `top` describes the products
+// (strided pointers or a device item array, plan = top_slot); chunk c0
+// starts at product c0 of it.
+static gf2x_status run_split_on(gf2x_ctx *ctx, uint32_t top_slot, uint32_t *ws, size_t ws_bytes,
+                                const LaunchArgs &top, size_t count, bool persistent, cudaStream_t stream)
 {
     auto ch = ctx->child_of.find(top_slot);
     if (ch == ctx->child_of.end())
@@ -458,14 +459,15 @@ static gf2x_status run_split_on(gf2x_ctx *ctx, uint32_t top_slot, uint32_t *ws, 
     const size_t top_smem = 4ull * T.smem_words;
     for (size_t c0 = 0; c0 < count; c0 += chunk) {
         const size_t k = std::min(chunk, count - c0);
-        LaunchArgs ta;
-        memset(&ta, 0, sizeof(ta));
-        ta.plans = ctx->plans_dev;
-        ta.base = DevItem{a + c0 * stride_in, b + c0 * stride_in, out + c0 * stride_out, top_slot, flags};
-        ta.stride_in = stride_in;
-        ta.stride_out = stride_out;
+        LaunchArgs ta = top;
+        if (ta.mode == kItemsStrided) {
+            ta.base.a += c0 * ta.stride_in;
+            ta.base.b += c0 * ta.stride_in;
+            ta.base.out += c0 * ta.stride_out;
+        } else {
+            ta.items += c0;
+        }
         ta.count = (uint32_t)k;
-        ta.mode = kItemsStrided;
         ta.err = ctx->err_dev;
         ta.persistent = persistent ? 1u : 0u;
         const unsigned tgrid = (unsigned)(persistent ? std::min<size_t>(k, 4ull * ctx->sm_count) : k);
@@ -493,9 +495,8 @@ static gf2x_status run_split_on(gf2x_ctx *ctx, uint32_t top_slot, uint32_t *ws, 
     return GF2X_OK;
 }
 
-static gf2x_status run_split(gf2x_ctx *ctx, uint32_t top_slot, uint64_t *out, const uint64_t *a, const uint64_t *b,
-                             size_t count, size_t stride_in, size_t stride_out, uint32_t flags, bool persistent,
-                             cudaStream_t stream)
+static gf2x_status run_split_args(gf2x_ctx *ctx, uint32_t top_slot, const LaunchArgs &top, size_t count,
+                                  bool persistent, cudaStream_t stream)
 {
     const GPlan &T = ctx->plans_host[top_slot];
     const size_t per = 4ull * T.lev[0].nch * 2ull * T.lev[0].E;
@@ -510,8 +511,7 @@ static gf2x_status run_split(gf2x_ctx *ctx, uint32_t top_slot, uint64_t *out, co
         if (e != cudaSuccess)
             return cuda_fail(ctx, e, "workspace ordering");
     }
-    st = run_split_on(ctx, top_slot, ctx->ws, ctx->ws_bytes, out, a, b, count, stride_in, stride_out, flags,
-                      persistent, stream);
+    st = run_split_on(ctx, top_slot, ctx->ws, ctx->ws_bytes, top, count, persistent, stream);
     if (st != GF2X_OK)
         return st;
     cudaError_t e = cudaEventRecord(ctx->ws_done, stream);
@@ -520,6 +520,20 @@ static gf2x_status run_split(gf2x_ctx *ctx, uint32_t top_slot, uint64_t *out, co
     ctx->ws_used = true;
     ctx->ws_stream = stream;
     return GF2X_OK;
+}
+
+static gf2x_status run_split(gf2x_ctx *ctx, uint32_t top_slot, uint64_t *out, const uint64_t *a, const uint64_t *b,
+                             size_t count, size_t stride_in, size_t stride_out, uint32_t flags, bool persistent,
+                             cudaStream_t stream)
+{
+    LaunchArgs ta;
+    memset(&ta, 0, sizeof(ta));
+    ta.plans = ctx->plans_dev;
+    ta.base = DevItem{a, b, out, top_slot, flags};
+    ta.stride_in = stride_in;
+    ta.stride_out = stride_out;
+    ta.mode = kItemsStrided;
+    return run_split_args(ctx, top_slot, ta, count, persistent, stream);
 }
 
 static gf2x_status one_product(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n,
@@ -698,10 +712,9 @@ extern "C" gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, s
         st = plan_for(ctx, it.n, s, &slot);
         if (st != GF2X_OK)
             return st;
-        if (ctx->plans_host[slot].split)
-            return fail(ctx, GF2X_EUNSUPPORTED, "split plans run through gf2x_mul_strided / gf2x_mul only");
         dv[i] = DevItem{it.a, it.b, it.out, slot, it.flags};
-        Ss[i] = ctx->plans_host[slot].S;
+        // launch groups: one per leaf size for in-CTA plans, one per plan for split plans
+        Ss[i] = ctx->plans_host[slot].split ? (0x80000000u | slot) : ctx->plans_host[slot].S;
     }
     // group by leaf size (one launch per group), largest n first if asked
     std::vector<size_t> order(count);
@@ -732,6 +745,20 @@ extern "C" gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, s
     while (g0 < count) {
         const uint32_t S = Ss[order[g0]];
         size_t g1 = g0;
+        if (S & 0x80000000u) {   // a split plan: its three launches over this group's items
+            while (g1 < count && Ss[order[g1]] == S)
+                ++g1;
+            LaunchArgs ta;
+            memset(&ta, 0, sizeof(ta));
+            ta.plans = ctx->plans_dev;
+            ta.items = stg->dev + g0;
+            ta.mode = kItemsArray;
+            st = run_split_args(ctx, S & 0x7fffffffu, ta, g1 - g0, persistent, s);
+            if (st != GF2X_OK)
+                return st;
+            g0 = g1;
+            continue;
+        }
         unsigned threads = 0;
         uint32_t smem_words = 0;
         while (g1 < count && Ss[order[g1]] == S) {
