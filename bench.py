@@ -653,6 +653,21 @@ def run_c5(device, requests):
         arr = wl.poisson_arrivals(wk.seed + int(f * 100), len(sizes), f * cap)
         r = srv.run(reqs, arr)
         out["loads"][str(f)] = dict(r.summary(), offered_per_s=f * cap)
+    # size-aware server: one queue, tuned plan and stream pair per size, so
+    # that sizes overlap on the GPU, each with its own plan's shape
+    sa_plans = autotune.best_plans(autotune.packaged_log(), list(weights), 512, allow_split=False)
+    sa = serve.SizeAwareServer(sa_plans, budget, max_batch=2048, streams_per_size=2, device=device)
+    sa_closed = sa.run(reqs, np.zeros(len(sizes)))
+    sa_cap = sa_closed.completed / sa_closed.wall_s
+    out["size_aware"] = {"plans": {str(k): v for k, v in sa_plans.items()}, "closed_loop": sa_closed.summary(),
+                         "loads": {}}
+    for f in (0.5, 0.8, 0.95, 1.2):
+        arr = wl.poisson_arrivals(wk.seed + 200 + int(f * 100), len(sizes), f * sa_cap)
+        r = sa.run(reqs, arr)
+        out["size_aware"]["loads"][str(f)] = dict(r.summary(), offered_per_s=f * sa_cap)
+    for c in sa.ctx.values():
+        c.sync_status()
+    sa.close()
     # a tight budget (4 MiB of output slots): admission has to wait for retirements
     tight = serve.Server(ctx, weights, 4 << 20, max_batch=2048, streams=3, use_graphs=True)
     arr = wl.poisson_arrivals(wk.seed + 95, len(sizes), 0.95 * cap)

@@ -188,6 +188,20 @@ def guided_search(tuner: "Autotuner", n: int, batch: int, model=None, k: int = 1
     return tuner.search(n, batch, model.rank(n, batch, cands)[:k])
 
 
+def best_plans(records: list, sizes, batch: int, allow_split: bool = True) -> dict:
+    """Fastest measured plan of every size at the batch bucket nearest `batch`."""
+    out = {}
+    for n in sizes:
+        recs = [r for r in records if r["n"] == n
+                and (allow_split or r["spec"].split("/")[5:6] != ["1"])]
+        if not recs:
+            continue
+        near = min(abs(math.log2(r["batch"]) - math.log2(batch)) for r in recs)
+        recs = [r for r in recs if abs(math.log2(r["batch"]) - math.log2(batch)) == near]
+        out[n] = min(recs, key=lambda r: r["ms"] / r["batch"])["spec"]
+    return out
+
+
 def mixed_plan_sets(records: list, weights: dict, batch: int, top: int = 3) -> list:
     """Candidate plan sets for ONE launch over several sizes, from a timing log.
 

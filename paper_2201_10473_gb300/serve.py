@@ -12,8 +12,10 @@ the device.  The loop
   * retires batches as their events complete, freeing their slots so that
     waiting requests are admitted while other batches are still running.
 
-The plain baseline launches one product per request (one CTA each), on the
-same streams.  Latency is completion time (event observed by the loop)
+SizeAwareServer keeps one queue, one tuned plan and its own streams per
+size, so that launches of different sizes run concurrently, each with the
+shared memory and CTA size of its own plan.  The plain baseline launches one
+product per request (one CTA each), on the same streams.  Latency is completion time (event observed by the loop)
 minus arrival time.
 """
 from __future__ import annotations
@@ -236,6 +238,145 @@ class Server:
                 batches += 1
                 batch_sum += k
                 progressed = True
+            if not progressed:
+                if inflight:
+                    time.sleep(2e-6)
+                elif nxt < N:
+                    time.sleep(max(0.0, min(1e-4, arr[nxt] - (time.perf_counter() - t0))))
+        wall = float(done_t.max() - arr[0]) if N else 0.0
+        return ServeResult(done_t - arrivals, wall, completed, batches, batch_sum / max(1, batches), max_inflight,
+                           waits)
+
+
+class SizeAwareServer:
+    """Continuous batching with one queue, one plan and one set of streams per
+    size: every size runs its own tuned (in-CTA) plan in graph-captured
+    persistent launches, and launches of different sizes overlap on the GPU.
+    Admission, slots and retirement as in Server."""
+
+    def __init__(self, plans: dict, budget_bytes: int, max_batch: int = 2048, streams_per_size: int = 2,
+                 min_bucket: int = 32, device: int = 0):
+        import torch
+        self.torch = torch
+        self.sizes = sorted(plans)
+        self.max_batch = max_batch
+        self.pool = SlotPool({n: 1 for n in self.sizes}, budget_bytes)
+        self.ctx = {}
+        for n in self.sizes:
+            c = gf2x.Context(device, plan_db=None)
+            c.set_plan(n, plans[n])
+            c.prepare([n])
+            self.ctx[n] = c
+        self.streams = {n: [torch.cuda.Stream() for _ in range(streams_per_size)] for n in self.sizes}
+        self.items_host = {(n, s): torch.zeros((max_batch, 4), dtype=torch.int64).pin_memory()
+                           for n in self.sizes for s in range(streams_per_size)}
+        self.items_dev = {k: torch.zeros((max_batch, 4), dtype=torch.int64, device="cuda") for k in self.items_host}
+        self.buckets = []
+        b = min_bucket
+        while b < max_batch:
+            self.buckets.append(b)
+            b *= 2
+        self.buckets.append(max_batch)
+        self.graphs = {}
+        for (n, s), host in self.items_host.items():
+            host.zero_()
+            st = self.streams[n][s]
+            with torch.cuda.stream(st):
+                self._launch(n, s, self.buckets[0])
+            torch.cuda.synchronize()
+            for B in self.buckets:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=st):
+                    self._launch(n, s, B)
+                self.graphs[(n, s, B)] = g
+        torch.cuda.synchronize()
+
+    def close(self):
+        for c in self.ctx.values():
+            c.close()
+
+    def _launch(self, n: int, s: int, count: int):
+        torch = self.torch
+        self.items_dev[(n, s)][:count].copy_(self.items_host[(n, s)][:count], non_blocking=True)
+        self.ctx[n].mul_batched_device(self.items_dev[(n, s)], count, persistent=True,
+                                       stream=torch.cuda.current_stream())
+
+    def _bucket(self, k: int) -> int:
+        for b in self.buckets:
+            if b >= k:
+                return b
+        return self.buckets[-1]
+
+    def run(self, reqs: RequestSet, arrivals: np.ndarray, collect=None) -> ServeResult:
+        torch = self.torch
+        N = len(reqs)
+        order = np.argsort(arrivals, kind="stable")
+        arr = arrivals[order]
+        queues = {n: deque() for n in self.sizes}
+        inflight = deque()        # (n, stream index, event, reqs, addrs)
+        free = {n: deque(range(len(self.streams[n]))) for n in self.sizes}
+        done_t = np.zeros(N)
+        nxt = completed = batches = batch_sum = waits = max_inflight = 0
+        t0 = time.perf_counter()
+        while completed < N:
+            now = time.perf_counter() - t0
+            while nxt < N and arr[nxt] <= now:
+                r = int(order[nxt])
+                queues[int(reqs.sizes[r])].append(r)
+                nxt += 1
+            progressed = False
+            # retire every finished batch (any order: sizes run independently)
+            if inflight:
+                keep = deque()
+                for item in inflight:
+                    n, s, ev, rs, addrs = item
+                    if ev.query():
+                        done_t[rs] = time.perf_counter() - t0
+                        if collect is not None:
+                            collect(rs, addrs, reqs.sizes[rs])
+                        for ad in addrs:
+                            self.pool.give(n, int(ad))
+                        completed += len(rs)
+                        free[n].append(s)
+                        progressed = True
+                    else:
+                        keep.append(item)
+                inflight = keep
+            for n in self.sizes:
+                q = queues[n]
+                while free[n] and q:
+                    rs_l, addr_l = [], []
+                    while q and len(rs_l) < self.max_batch:
+                        ad = self.pool.take(n)
+                        if ad is None:
+                            waits += 1
+                            break
+                        rs_l.append(q.popleft())
+                        addr_l.append(ad)
+                    if not rs_l:
+                        break
+                    s = free[n].popleft()
+                    rs = np.array(rs_l, dtype=np.int64)
+                    addrs = np.array(addr_l, dtype=np.int64)
+                    pa, pb = reqs.ptrs(rs)
+                    k = len(rs)
+                    B = self._bucket(k)
+                    h = self.items_host[(n, s)].numpy()
+                    h[:k, 0] = pa
+                    h[:k, 1] = pb
+                    h[:k, 2] = addrs
+                    h[:k, 3] = n | (1 << 32)
+                    h[k:B] = 0
+                    st = self.streams[n][s]
+                    with torch.cuda.stream(st):
+                        self.graphs[(n, s, B)].replay()
+                        ev = torch.cuda.Event()
+                        ev.record(st)
+                    inflight.append((n, s, ev, rs, addrs))
+                    max_inflight = max(max_inflight, len(inflight))
+                    batches += 1
+                    batch_sum += k
+                    progressed = True
             if not progressed:
                 if inflight:
                     time.sleep(2e-6)

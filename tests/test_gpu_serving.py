@@ -79,3 +79,34 @@ def test_plain_baseline_serves_everything():
             assert torch.equal(ctx.mulmod(reqs.a[n][i], reqs.b[n][i], n), results[r])
     finally:
         ctx.close()
+
+
+def test_size_aware_server_identical_alone_and_in_the_mix():
+    from paper_2201_10473_gb300 import Context, autotune, serve
+    plans = autotune.best_plans(autotune.packaged_log(), SIZES, 512, allow_split=False)
+    assert set(plans) == set(SIZES)
+    srv = serve.SizeAwareServer(plans, serve.default_budget(SIZES, 300), max_batch=256, streams_per_size=2)
+    ctx = Context(0)
+    try:
+        count = 1500
+        sizes = wl.uniform_choice(wl.BASE_SEED + 7, count, SIZES)
+        reqs = serve.make_requests(sizes, lambda n, c: wl.dense_pair(wl.BASE_SEED + 7 + n, n, c))
+        arrivals = wl.poisson_arrivals(wl.BASE_SEED + 7, count, 2e5)
+        results = {}
+        res = srv.run(reqs, arrivals, collect=_collector(reqs, srv.pool, results))
+        for c in srv.ctx.values():
+            c.sync_status()
+        assert res.completed == count and len(results) == count and res.admission_waits > 0
+        for r in range(count):
+            n = sizes[r]
+            i = int(reqs.index[r])
+            assert torch.equal(ctx.mulmod(reqs.a[n][i], reqs.b[n][i], n), results[r]), r
+        for r in range(0, count, 101):
+            n = sizes[r]
+            i = int(reqs.index[r])
+            a = reqs.a[n][i].cpu().numpy().view(np.uint64)
+            b = reqs.b[n][i].cpu().numpy().view(np.uint64)
+            assert np.array_equal(results[r].cpu().numpy().view(np.uint64), oracle.mulmod(a, b, n))
+    finally:
+        ctx.close()
+        srv.close()
