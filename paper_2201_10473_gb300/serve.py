@@ -52,6 +52,11 @@ class RequestSet:
             pb[sel] = self.b[int(n)].data_ptr() + self.index[rs[sel]] * 8 * L
         return pa, pb
 
+    def ptrs_of_size(self, n: int, rs: np.ndarray):
+        """Device addresses of the operands of requests rs, all of size n."""
+        off = self.index[rs] * (8 * gf2x.limbs(int(n)))
+        return self.a[int(n)].data_ptr() + off, self.b[int(n)].data_ptr() + off
+
 
 def make_requests(sizes, operand_fn) -> RequestSet:
     """operand_fn(n, count) -> (a, b) numpy uint64 arrays of `count` rows."""
@@ -69,30 +74,52 @@ def make_requests(sizes, operand_fn) -> RequestSet:
 
 
 class SlotPool:
-    """Output slots of every size class carved from one arena of budget_bytes."""
+    """Output slots of every size class carved from one arena of budget_bytes.
 
-    def __init__(self, sizes: dict, budget_bytes: int):
+    The free slots of a size are a stack of addresses (free[n][:top[n]]), so
+    that a batch takes or returns all of its slots in one array operation."""
+
+    def __init__(self, sizes: dict, budget_bytes: int, device="cuda"):
         import torch
         total_w = sum(sizes.values())
-        self.arena = torch.empty(max(1, budget_bytes // 8), dtype=torch.int64, device="cuda")
+        self.arena = torch.empty(max(1, budget_bytes // 8), dtype=torch.int64, device=device)
         base = self.arena.data_ptr()
         self.free = {}
+        self.top = {}
         self.slot_limbs = {}
         off = 0
         for n, w in sorted(sizes.items()):
             L = (gf2x.limbs(n) + 1) // 2 * 2           # 16-byte aligned slots
             share = int(budget_bytes * w / total_w) // (8 * L)
             self.slot_limbs[n] = L
-            self.free[n] = deque(base + 8 * (off + i * L) for i in range(share))
+            self.free[n] = base + 8 * (off + L * np.arange(share, dtype=np.int64))
+            self.top[n] = share
             off += share * L
-        self.capacity = {n: len(q) for n, q in self.free.items()}
+        self.capacity = dict(self.top)
+
+    def available(self, n: int) -> int:
+        return self.top.get(n, 0)
+
+    def take_many(self, n: int, k: int) -> np.ndarray:
+        """k free slots of size n (k <= available(n))."""
+        t = self.top[n]
+        if k > t:
+            raise ValueError("not enough free slots")
+        self.top[n] = t - k
+        return self.free[n][t - k: t].copy()
+
+    def give_many(self, n: int, addrs: np.ndarray):
+        t = self.top[n]
+        self.free[n][t: t + len(addrs)] = addrs
+        self.top[n] = t + len(addrs)
 
     def take(self, n: int):
-        q = self.free.get(n)
-        return q.popleft() if q else None
+        if self.top.get(n, 0) == 0:
+            return None
+        return int(self.take_many(n, 1)[0])
 
     def give(self, n: int, addr: int):
-        self.free[n].append(addr)
+        self.give_many(n, np.array([addr], dtype=np.int64))
 
 
 @dataclass
@@ -173,58 +200,55 @@ class Server:
         N = len(reqs)
         order = np.argsort(arrivals, kind="stable")
         arr = arrivals[order]
-        queue = deque()
+        osz = reqs.sizes[order]
+        head = 0                  # order[head:arrived] is the admission queue (FIFO)
         inflight = deque()        # (stream, event, reqs, addrs)
         free_streams = deque(range(self.nstreams))
         done_t = np.zeros(N)
-        nxt = 0
-        completed = 0
-        batches = 0
-        batch_sum = 0
-        waits = 0
-        max_inflight = 0
+        completed = batches = batch_sum = waits = max_inflight = 0
         t0 = time.perf_counter()
         while completed < N:
-            now = time.perf_counter() - t0
-            while nxt < N and arr[nxt] <= now:
-                queue.append(int(order[nxt]))
-                nxt += 1
+            arrived = int(np.searchsorted(arr, time.perf_counter() - t0, side="right"))
             progressed = False
             while inflight and inflight[0][1].query():
                 s, ev, rs, addrs = inflight.popleft()
-                tdone = time.perf_counter() - t0
-                done_t[rs] = tdone
+                done_t[rs] = time.perf_counter() - t0
                 if collect is not None:
                     collect(rs, addrs, reqs.sizes[rs])
-                for r, ad in zip(rs, addrs):
-                    self.pool.give(int(reqs.sizes[r]), int(ad))
+                szs = reqs.sizes[rs]
+                for n in np.unique(szs):
+                    self.pool.give_many(int(n), addrs[szs == n])
                 completed += len(rs)
                 free_streams.append(s)
                 progressed = True
-            while free_streams and queue:
-                rs_l, addr_l = [], []
-                while queue and len(rs_l) < self.max_batch:
-                    r = queue[0]
-                    ad = self.pool.take(int(reqs.sizes[r]))
-                    if ad is None:           # no memory for the head request: wait for a retirement
-                        waits += 1
-                        break
-                    queue.popleft()
-                    rs_l.append(r)
-                    addr_l.append(ad)
-                if not rs_l:
+            while free_streams and head < arrived:
+                # admit in arrival order up to the first request whose size has no free slot
+                cand = osz[head: min(arrived, head + self.max_batch)]
+                k = len(cand)
+                for n in np.unique(cand):
+                    pos = np.flatnonzero(cand == n)
+                    avail = self.pool.available(int(n))
+                    if len(pos) > avail:
+                        k = min(k, int(pos[avail]))
+                if k < len(cand):
+                    waits += 1
+                if k == 0:
                     break
+                rs = order[head: head + k]
+                szs = cand[:k]
+                addrs = np.empty(k, dtype=np.int64)
+                for n in np.unique(szs):
+                    sel = szs == n
+                    addrs[sel] = self.pool.take_many(int(n), int(sel.sum()))
+                head += k
                 s = free_streams.popleft()
-                rs = np.array(rs_l, dtype=np.int64)
-                addrs = np.array(addr_l, dtype=np.int64)
                 pa, pb = reqs.ptrs(rs)
-                k = len(rs)
                 B = self._bucket(k) if self.use_graphs else k
                 h = self.items_host[s].numpy()
                 h[:k, 0] = pa
                 h[:k, 1] = pb
                 h[:k, 2] = addrs
-                h[:k, 3] = reqs.sizes[rs] | (1 << 32)      # n | GF2X_REDUCE << 32
+                h[:k, 3] = szs | (1 << 32)      # n | GF2X_REDUCE << 32
                 h[k:B] = 0
                 with torch.cuda.stream(self.streams[s]):
                     if self.use_graphs:
@@ -241,8 +265,8 @@ class Server:
             if not progressed:
                 if inflight:
                     time.sleep(2e-6)
-                elif nxt < N:
-                    time.sleep(max(0.0, min(1e-4, arr[nxt] - (time.perf_counter() - t0))))
+                elif head < N:
+                    time.sleep(max(0.0, min(1e-4, arr[head] - (time.perf_counter() - t0))))
         wall = float(done_t.max() - arr[0]) if N else 0.0
         return ServeResult(done_t - arrivals, wall, completed, batches, batch_sum / max(1, batches), max_inflight,
                            waits)
@@ -312,30 +336,34 @@ class SizeAwareServer:
         N = len(reqs)
         order = np.argsort(arrivals, kind="stable")
         arr = arrivals[order]
-        queues = {n: deque() for n in self.sizes}
-        inflight = deque()        # (n, stream index, event, reqs, addrs)
+        # per size: its requests in arrival order, their arrival times, and a queue head
+        ids = {n: order[reqs.sizes[order] == n] for n in self.sizes}
+        tarr = {n: arr[reqs.sizes[order] == n] for n in self.sizes}
+        head = {n: 0 for n in self.sizes}
+        if sum(len(v) for v in ids.values()) != N:
+            raise ValueError("a request has a size this server has no plan for")
+        # a batch may take at most its share of the size's slots, so that every
+        # stream of the size can have a batch in flight while the host fills the
+        # next; the budget then bounds the batch size and admission never waits
+        cap = {n: max(1, min(self.max_batch, self.pool.capacity[n] // len(self.streams[n]))) for n in self.sizes}
+        inflight = []             # (n, stream index, event, reqs, addrs)
         free = {n: deque(range(len(self.streams[n]))) for n in self.sizes}
         done_t = np.zeros(N)
-        nxt = completed = batches = batch_sum = waits = max_inflight = 0
+        completed = batches = batch_sum = waits = max_inflight = 0
         t0 = time.perf_counter()
         while completed < N:
             now = time.perf_counter() - t0
-            while nxt < N and arr[nxt] <= now:
-                r = int(order[nxt])
-                queues[int(reqs.sizes[r])].append(r)
-                nxt += 1
             progressed = False
             # retire every finished batch (any order: sizes run independently)
             if inflight:
-                keep = deque()
+                keep = []
                 for item in inflight:
                     n, s, ev, rs, addrs = item
                     if ev.query():
                         done_t[rs] = time.perf_counter() - t0
                         if collect is not None:
                             collect(rs, addrs, reqs.sizes[rs])
-                        for ad in addrs:
-                            self.pool.give(n, int(ad))
+                        self.pool.give_many(n, addrs)
                         completed += len(rs)
                         free[n].append(s)
                         progressed = True
@@ -343,23 +371,19 @@ class SizeAwareServer:
                         keep.append(item)
                 inflight = keep
             for n in self.sizes:
-                q = queues[n]
-                while free[n] and q:
-                    rs_l, addr_l = [], []
-                    while q and len(rs_l) < self.max_batch:
-                        ad = self.pool.take(n)
-                        if ad is None:
-                            waits += 1
-                            break
-                        rs_l.append(q.popleft())
-                        addr_l.append(ad)
-                    if not rs_l:
+                arrived = int(np.searchsorted(tarr[n], now, side="right"))
+                while free[n] and head[n] < arrived:
+                    avail = self.pool.available(n)
+                    k = min(arrived - head[n], cap[n], avail)
+                    if k < min(arrived - head[n], cap[n]):
+                        waits += 1
+                    if k == 0:
                         break
+                    rs = ids[n][head[n]: head[n] + k]
+                    head[n] += k
+                    addrs = self.pool.take_many(n, k)
                     s = free[n].popleft()
-                    rs = np.array(rs_l, dtype=np.int64)
-                    addrs = np.array(addr_l, dtype=np.int64)
-                    pa, pb = reqs.ptrs(rs)
-                    k = len(rs)
+                    pa, pb = reqs.ptrs_of_size(n, rs)
                     B = self._bucket(k)
                     h = self.items_host[(n, s)].numpy()
                     h[:k, 0] = pa
@@ -380,8 +404,10 @@ class SizeAwareServer:
             if not progressed:
                 if inflight:
                     time.sleep(2e-6)
-                elif nxt < N:
-                    time.sleep(max(0.0, min(1e-4, arr[nxt] - (time.perf_counter() - t0))))
+                else:
+                    nxt = min((tarr[n][head[n]] for n in self.sizes if head[n] < len(ids[n])), default=None)
+                    if nxt is not None:
+                        time.sleep(max(0.0, min(1e-4, nxt - (time.perf_counter() - t0))))
         wall = float(done_t.max() - arr[0]) if N else 0.0
         return ServeResult(done_t - arrivals, wall, completed, batches, batch_sum / max(1, batches), max_inflight,
                            waits)

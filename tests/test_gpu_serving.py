@@ -96,7 +96,10 @@ def test_size_aware_server_identical_alone_and_in_the_mix():
         res = srv.run(reqs, arrivals, collect=_collector(reqs, srv.pool, results))
         for c in srv.ctx.values():
             c.sync_status()
-        assert res.completed == count and len(results) == count and res.admission_waits > 0
+        assert res.completed == count and len(results) == count
+        # the small budget bounds every batch to its size's share of the slots
+        cap = max(srv.pool.capacity[n] // 2 for n in SIZES)
+        assert res.batches >= count / cap and res.mean_batch <= cap
         for r in range(count):
             n = sizes[r]
             i = int(reqs.index[r])
