@@ -1,0 +1,378 @@
+// Bitsliced leaf experiment: the 192 x 192-bit leaf products of a shared-memory
+// leaf pass computed 32 at a time in bitsliced form (word t of a group = the
+// coefficient of X^t of 32 leaves), against the library's comb leaf (one leaf
+// per thread).  A group is transposed in (32 x 32 bit transposes), multiplied
+// as 32 x 32-coefficient blocks (one LOP3 per AND-XOR of 32 leaves, no shifts
+// and no masks), and transposed out.  Two block schedules:
+//   k3k2  3-way then 2-way Karatsuba (Sec. 3, k = 3 and k = 2): 18 blocks per
+//         group, evaluation, block products, interpolation, four phases;
+//   diag  6 x 6 schoolbook, diagonals split into tasks of at most 3 blocks:
+//         36 blocks, no evaluation or interpolation phases.
+// Each CTA loads 32G leaves once and repeats the leaf pass over shared memory;
+// every result is checked against a bit-by-bit product on the host first.
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../csrc/fused.cuh"
+
+using gf2x::comb;
+
+#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { printf("CUDA %s at %d\n", cudaGetErrorString(e_), __LINE__); exit(1);} } while (0)
+
+constexpr int S = 6, LW = 12;
+
+__host__ __device__ __forceinline__ uint32_t sel_bits(uint32_t x, uint32_t y, uint32_t m) { return (x & m) | (y & ~m); }
+
+__device__ __forceinline__ void transpose32(uint32_t (&r)[32])
+{
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        const uint32_t x = r[l], y = r[l + 16];
+        r[l] = __byte_perm(x, y, 0x5410);
+        r[l + 16] = __byte_perm(x, y, 0x7632);
+    }
+#pragma unroll
+    for (int l0 = 0; l0 < 32; l0 += 16)
+#pragma unroll
+        for (int l = l0; l < l0 + 8; ++l) {
+            const uint32_t x = r[l], y = r[l + 8];
+            r[l] = __byte_perm(x, y, 0x6240);
+            r[l + 8] = __byte_perm(x, y, 0x7351);
+        }
+#pragma unroll
+    for (int j = 4; j >= 1; j >>= 1) {
+        const uint32_t m = j == 4 ? 0x0F0F0F0Fu : (j == 2 ? 0x33333333u : 0x55555555u);
+#pragma unroll
+        for (int l = 0; l < 32; ++l) {
+            if (l & j) continue;
+            const uint32_t x = r[l], y = r[l + j];
+            r[l] = sel_bits(x, y << j, m);
+            r[l + j] = sel_bits(x >> j, y, m);
+        }
+    }
+}
+
+
+__device__ __forceinline__ void bsmul32_stream(const uint32_t (&a)[32], const uint32_t *brow, uint32_t (&q)[63])
+{
+#pragma unroll
+    for (int k = 0; k < 63; ++k) q[k] = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t bj = brow[j];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) q[i + j] ^= a[i] & bj;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void t_in(uint32_t *sm, int ab, int abstride)
+{
+    for (int task = threadIdx.x; task < G * LW; task += blockDim.x) {
+        const int g = task / LW, w = task % LW;
+        uint32_t r[32];
+#pragma unroll
+        for (int l = 0; l < 32; ++l) r[l] = sm[(32 * g + l) * LW + w];
+        transpose32(r);
+        uint32_t *dst = sm + ab + abstride * g + 33 * w;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) dst[k] = r[k];
+    }
+}
+
+// ---------------- K3 o K2 on 192 coefficients, v2
+// group area: AB 12 x 33 | E 24 x 33 (U 5 x 132 overlays it) | Q 18 x 65
+template <int G>
+struct Lay {
+    static constexpr int ab = 32 * G * LW;
+    static constexpr int per = 396 + 792 + 1170;
+    static constexpr int total = ab + per * G;
+};
+
+// row of operand op (0 A, 1 B) for K3 child c, K2 child d, relative to the group area
+__device__ __forceinline__ int row_of(int op, int c, int d)
+{
+    if (c < 3 && d < 2) return 33 * (6 * op + 2 * c + d);
+    const int idx = c < 3 ? c : 3 + 3 * (c - 3) + d;
+    return 396 + 33 * (12 * op + idx);
+}
+
+template <int G>
+__device__ void bs_pass(uint32_t *sm)
+{
+    using L = Lay<G>;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    t_in<G>(sm, L::ab, L::per);
+    __syncthreads();
+    // evaluation: 12 computed rows per operand
+    for (int task = tid; task < G * 2 * 16 * 32; task += nt) {
+        const int t = task & 31, idx = (task >> 5) & 15, op = (task >> 9) & 1, g = task >> 10;
+        if (idx >= 12) continue;
+        uint32_t *grp = sm + L::ab + L::per * g;
+        const uint32_t *base = grp + 33 * 6 * op;
+        uint32_t v;
+        if (idx < 3) {
+            v = base[33 * (2 * idx) + t] ^ base[33 * (2 * idx + 1) + t];
+        } else {
+            const int c = 3 + (idx - 3) / 3, d = (idx - 3) % 3;
+            const int p = c == 5 ? 1 : 0, q = c == 3 ? 1 : 2;
+            if (d < 2) v = base[33 * (2 * p + d) + t] ^ base[33 * (2 * q + d) + t];
+            else v = base[33 * (2 * p) + t] ^ base[33 * (2 * p + 1) + t] ^ base[33 * (2 * q) + t] ^ base[33 * (2 * q + 1) + t];
+        }
+        grp[396 + 33 * (12 * op + idx) + t] = v;
+    }
+    __syncthreads();
+    // block products
+    for (int task = tid; task < G * 18; task += nt) {
+        const int g = task / 18, cd = task - 18 * g, c = cd / 3, d = cd - 3 * c;
+        const uint32_t *grp = sm + L::ab + L::per * g;
+        const uint32_t *arow = grp + row_of(0, c, d), *brow = grp + row_of(1, c, d);
+        uint32_t a[32], q[63];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) a[t] = arow[t];
+        bsmul32_stream(a, brow, q);
+        uint32_t *dst = sm + L::ab + L::per * g + 1188 + 65 * cd;
+#pragma unroll
+        for (int k = 0; k < 63; ++k) dst[k] = q[k];
+    }
+    __syncthreads();
+    // K2 then K3 interpolation into U_e (e = 0..4), U row index t stored at t + t/32
+    for (int task = tid; task < G * 128; task += nt) {
+        const int u = task & 127, g = task >> 7;
+        uint32_t *grp = sm + L::ab + L::per * g;
+        const uint32_t *Q = grp + 1188;
+        uint32_t R[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const uint32_t *q0 = Q + 65 * (3 * c), *q1 = q0 + 65, *q2 = q0 + 130;
+            uint32_t v = 0;
+            if (u < 63) v ^= q0[u];
+            if (u >= 32 && u < 95) v ^= q0[u - 32] ^ q1[u - 32] ^ q2[u - 32];
+            if (u >= 64 && u < 127) v ^= q1[u - 64];
+            R[c] = v;
+        }
+        uint32_t *U = grp + 396;
+        const int pu = u + (u >> 5);
+        U[0 * 132 + pu] = R[0];
+        U[1 * 132 + pu] = R[3] ^ R[0] ^ R[1];
+        U[2 * 132 + pu] = R[4] ^ R[0] ^ R[1] ^ R[2];
+        U[3 * 132 + pu] = R[5] ^ R[1] ^ R[2];
+        U[4 * 132 + pu] = R[2];
+    }
+    __syncthreads();
+    // C block w = sum over e of U_e block (w - 2e), 0 <= w - 2e <= 3
+    for (int task = tid; task < G * LW; task += nt) {
+        const int g = task / LW, w = task - LW * g;
+        const uint32_t *U = sm + L::ab + L::per * g + 396;
+        const int e0 = w <= 3 ? 0 : (w - 2) >> 1;      // smallest e with w - 2e <= 3
+        const uint32_t *u0 = U + 132 * e0 + 33 * (w - 2 * e0);
+        const bool two = e0 + 1 <= 4 && w - 2 * (e0 + 1) >= 0;
+        const uint32_t *u1 = U + 132 * (e0 + 1) + 33 * (two ? w - 2 * (e0 + 1) : 0);
+        const uint32_t m1 = two ? 0xFFFFFFFFu : 0u;
+        uint32_t r[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) r[k] = u0[k] ^ (u1[k] & m1);
+        transpose32(r);
+#pragma unroll
+        for (int l = 0; l < 32; ++l) sm[(32 * g + l) * LW + w] = r[l];
+    }
+    __syncthreads();
+}
+
+// ---------------- schoolbook over 6 x 6 blocks, diagonals split into tasks of <= 3 blocks
+template <int G>
+struct LayD {
+    static constexpr int ab = 32 * G * LW;
+    static constexpr int per = 396 + 16 * 65;
+    static constexpr int total = ab + per * G;
+};
+__constant__ int8_t kDiag[16][3] = {{0, 0, 0}, {1, 0, 1}, {2, 0, 2}, {3, 0, 1}, {3, 2, 3}, {4, 0, 2}, {4, 3, 4},
+                                    {5, 0, 2}, {5, 3, 5}, {6, 1, 3}, {6, 4, 5}, {7, 2, 3}, {7, 4, 5}, {8, 3, 5},
+                                    {9, 4, 5}, {10, 5, 5}};
+// tasks of diagonal k: first index and count
+__constant__ int8_t kDiagFirst[11] = {0, 1, 2, 3, 5, 7, 9, 11, 13, 14, 15};
+__constant__ int8_t kDiagCount[11] = {1, 1, 1, 2, 2, 2, 2, 2, 1, 1, 1};
+
+template <int G>
+__device__ void bsd_pass(uint32_t *sm)
+{
+    using L = LayD<G>;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    t_in<G>(sm, L::ab, L::per);
+    __syncthreads();
+    for (int task = tid; task < G * 16; task += nt) {
+        const int g = task >> 4, tk = task & 15;
+        const int k = kDiag[tk][0], i0 = kDiag[tk][1], i1 = kDiag[tk][2];
+        const uint32_t *A = sm + L::ab + L::per * g, *B = A + 6 * 33;
+        uint32_t q[63];
+#pragma unroll
+        for (int x = 0; x < 63; ++x) q[x] = 0;
+        for (int i = i0; i <= i1; ++i) {
+            uint32_t a[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) a[t] = A[33 * i + t];
+            const uint32_t *brow = B + 33 * (k - i);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const uint32_t bj = brow[j];
+#pragma unroll
+                for (int ii = 0; ii < 32; ++ii) q[ii + j] ^= a[ii] & bj;
+            }
+        }
+        uint32_t *dst = sm + L::ab + L::per * g + 396 + 65 * tk;
+#pragma unroll
+        for (int x = 0; x < 63; ++x) dst[x] = q[x];
+    }
+    __syncthreads();
+    for (int task = tid; task < G * LW; task += nt) {
+        const int g = task / LW, w = task - LW * g;
+        const uint32_t *D = sm + L::ab + L::per * g + 396;
+        // rows of diagonal w (offset 0) and of diagonal w - 1 (offset 32)
+        const int fa = w <= 10 ? kDiagFirst[w] : 0, na = w <= 10 ? kDiagCount[w] : 0;
+        const int fb = w >= 1 ? kDiagFirst[w - 1] : 0, nb = w >= 1 ? kDiagCount[w - 1] : 0;
+        const uint32_t ma0 = na > 0 ? ~0u : 0u, ma1 = na > 1 ? ~0u : 0u, mb0 = nb > 0 ? ~0u : 0u, mb1 = nb > 1 ? ~0u : 0u;
+        const uint32_t *a0 = D + 65 * fa, *a1 = D + 65 * (fa + (na > 1)), *b0 = D + 65 * fb + 32, *b1 = D + 65 * (fb + (nb > 1)) + 32;
+        uint32_t r[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            uint32_t v = (a0[k] & ma0) ^ (a1[k] & ma1);
+            if (k <= 30) v ^= (b0[k] & mb0) ^ (b1[k] & mb1);
+            r[k] = v;
+        }
+        transpose32(r);
+#pragma unroll
+        for (int l = 0; l < 32; ++l) sm[(32 * g + l) * LW + w] = r[l];
+    }
+    __syncthreads();
+}
+
+__device__ void comb_pass(uint32_t *sm, int nleaf)
+{
+    for (int l = threadIdx.x; l < nleaf; l += blockDim.x) {
+        uint32_t a[S], b[S], c[2 * S];
+#pragma unroll
+        for (int i = 0; i < S; ++i) { a[i] = sm[l * LW + i]; b[i] = sm[l * LW + S + i]; }
+        comb<S>(a, b, c);
+#pragma unroll
+        for (int i = 0; i < 2 * S; ++i) sm[l * LW + i] = c[i];
+    }
+    __syncthreads();
+}
+
+// one pass of 32G leaves per CTA, loaded once; `reps` leaf passes over shared memory
+template <int G, int MODE>
+__global__ void __launch_bounds__(128, 1) kern(const uint32_t *in, uint32_t *out, int reps)
+{
+    extern __shared__ uint32_t sm[];
+    const int P = 32 * G;
+    const uint32_t *src = in + (size_t)blockIdx.x * P * LW;
+    for (int i = threadIdx.x; i < P * LW; i += blockDim.x) sm[i] = src[i];
+    __syncthreads();
+    for (int r = 0; r < reps; ++r) {
+        if (MODE == 0) comb_pass(sm, P); else if (MODE == 1) bs_pass<G>(sm); else bsd_pass<G>(sm);
+    }
+    uint32_t *dst = out + (size_t)blockIdx.x * P * LW;
+    for (int i = threadIdx.x; i < P * LW; i += blockDim.x) dst[i] = sm[i];
+}
+
+static void clmul_ref(const uint32_t *a, const uint32_t *b, uint32_t *c)
+{
+    memset(c, 0, 4 * LW);
+    for (int i = 0; i < 32 * S; ++i)
+        if ((b[i / 32] >> (i % 32)) & 1)
+            for (int k = 0; k < 32 * S; ++k)
+                if ((a[k / 32] >> (k % 32)) & 1) c[(i + k) / 32] ^= 1u << ((i + k) % 32);
+}
+
+
+template <int G, int MODE>
+static size_t smem_of() { return 4 * (MODE == 0 ? 32 * G * LW : MODE == 1 ? Lay<G>::total : LayD<G>::total); }
+
+template <int G, int MODE>
+static int occupancy(int threads)
+{
+    const size_t smem = smem_of<G, MODE>();
+    CK(cudaFuncSetAttribute(kern<G, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern<G, MODE>, threads, smem));
+    return per_sm;
+}
+
+template <int G, int MODE>
+static void launch(const uint32_t *din, uint32_t *dout, int grid, int reps)
+{
+    kern<G, MODE><<<grid, 128, smem_of<G, MODE>()>>>(din, dout, reps);
+    CK(cudaGetLastError());
+}
+
+template <int G, int MODE>
+static int check_and_time(const char *name)
+{
+    const int per_sm = occupancy<G, MODE>(128);
+    const int grid = 152 * per_sm;
+    const size_t nwords = (size_t)grid * 32 * G * LW;
+    std::vector<uint32_t> h(nwords), o(nwords);
+    uint64_t s = 0x9E3779B97F4A7C15ull ^ (G * 131 + MODE);
+    for (auto &x : h) { s ^= s << 13; s ^= s >> 7; s ^= s << 17; x = (uint32_t)(s >> 11); }
+    uint32_t *din, *dout;
+    CK(cudaMalloc(&din, 4 * nwords)); CK(cudaMalloc(&dout, 4 * nwords));
+    CK(cudaMemcpy(din, h.data(), 4 * nwords, cudaMemcpyHostToDevice));
+    launch<G, MODE>(din, dout, grid, 1);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(o.data(), dout, 4 * nwords, cudaMemcpyDeviceToHost));
+    int bad = 0;
+    const size_t nleaves = nwords / LW;
+    for (int l = 0; l < 3000; ++l) {
+        size_t leaf = (size_t)l * 7919 % nleaves;
+        uint32_t c[LW];
+        clmul_ref(&h[leaf * LW], &h[leaf * LW + S], c);
+        bad += memcmp(c, &o[leaf * LW], 4 * LW) != 0;
+    }
+    const int reps = 40;
+    launch<G, MODE>(din, dout, grid, reps);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0); cudaEventCreate(&e1);
+    cudaEventRecord(e0);
+    launch<G, MODE>(din, dout, grid, reps);
+    cudaEventRecord(e1);
+    CK(cudaEventSynchronize(e1));
+    float ms; cudaEventElapsedTime(&ms, e0, e1);
+    printf("%-10s G %2d smem %6zu ctas/sm %d: %3d bad of 3000, %.1f M leaves/s\n", name, G, smem_of<G, MODE>(), per_sm,
+           bad, (double)nleaves * reps / (ms * 1e-3) / 1e6);
+    CK(cudaFree(din)); CK(cudaFree(dout));
+    return bad ? 2 : 0;
+}
+
+template <int G, int MODE>
+static void prof_one()
+{
+    const int grid = 152 * occupancy<G, MODE>(128);
+    const size_t nwords = (size_t)grid * 32 * G * LW;
+    uint32_t *din, *dout;
+    CK(cudaMalloc(&din, 4 * nwords)); CK(cudaMalloc(&dout, 4 * nwords));
+    CK(cudaMemset(din, 0x5a, 4 * nwords));
+    launch<G, MODE>(din, dout, grid, 4);
+    CK(cudaDeviceSynchronize());
+    CK(cudaFree(din)); CK(cudaFree(dout));
+}
+
+int main(int argc, char **argv)
+{
+    if (argc > 1) {   // one launch of each kind, for a profiler
+        prof_one<7, 0>(); prof_one<7, 1>(); prof_one<8, 2>(); printf("ok\n"); return 0;
+    }
+    int rc = 0;
+    rc |= check_and_time<7, 0>("comb");
+    rc |= check_and_time<2, 0>("comb");
+    rc |= check_and_time<4, 1>("k3k2");
+    rc |= check_and_time<6, 1>("k3k2");
+    rc |= check_and_time<7, 1>("k3k2");
+    rc |= check_and_time<8, 1>("k3k2");
+    rc |= check_and_time<4, 2>("diag");
+    rc |= check_and_time<6, 2>("diag");
+    rc |= check_and_time<8, 2>("diag");
+    return rc;
+}
