@@ -184,6 +184,11 @@ class Server:
                 with torch.cuda.graph(g, stream=self.streams[s]):
                     self._launch(s, B)
                 self.graphs[(s, B)] = g
+        # one replay of every graph over empty items, so that no first replay
+        # (which uploads the graph) happens while requests wait
+        for (s, B), g in self.graphs.items():
+            with torch.cuda.stream(self.streams[s]):
+                g.replay()
         torch.cuda.synchronize()
 
     def _bucket(self, k: int) -> int:
@@ -313,6 +318,9 @@ class SizeAwareServer:
                 with torch.cuda.graph(g, stream=st):
                     self._launch(n, s, B)
                 self.graphs[(n, s, B)] = g
+        for (n, s, B), g in self.graphs.items():       # upload every graph (empty items)
+            with torch.cuda.stream(self.streams[n][s]):
+                g.replay()
         torch.cuda.synchronize()
 
     def close(self):
