@@ -5,7 +5,7 @@ It is trained on the autotuner's own timing log by the library's CUDA kernels
 (gf2x_mlp_grad / gf2x_mlp_adam, forward by gf2x_mlp_forward); torch only
 holds the device buffers.  Given a size and a batch it orders the candidate
 plans so that only the first few are measured; exhaustive measured search
-remains the fallback and the judge of its regret (evaluate_gain).
+remains the fallback and the measure of its regret (evaluate_gain).
 """
 from __future__ import annotations
 

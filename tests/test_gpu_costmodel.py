@@ -93,7 +93,7 @@ def test_learned_model_beats_unguided_search(holdout):
     """Trained by the CUDA kernels on the GB300 timing log of the other sizes,
     the network orders the held-out size's candidates so that a plan within 5%
     of the exhaustive best comes far earlier than in random order, and its top
-    10 are within 10% of the best (exhaustive search is the judge)."""
+    10 are within 10% of the best (exhaustive search gives the best)."""
     from paper_2201_10473_gb300 import autotune, costmodel
     r = costmodel.evaluate_gain(autotune.packaged_log(), holdout, 2048, k=10, steps=3000)
     assert r["model_measurements_to_5pct"] * 4 <= r["random_expected_measurements_to_5pct"], r
