@@ -314,6 +314,7 @@ def main(argv=None):
     p.add_argument("--from-log", default=None, help="re-measure only the best --top plans of this timing log "
                                                      "('packaged' = the shipped GB300 log)")
     p.add_argument("--top", type=int, default=60)
+    p.add_argument("--split-from", type=int, default=24000, help="also try split-top plans from this size on")
     a = p.parse_args(argv)
     prior = None
     if a.from_log:
@@ -325,7 +326,7 @@ def main(argv=None):
     for n in sizes:
         ctx = gf2x.Context()          # a fresh plan table per size
         tuner = Autotuner(ctx, a.log)
-        cands = candidate_specs(n, limit=a.limit)
+        cands = candidate_specs(n, limit=a.limit, split_from=a.split_from)
         if prior is not None:
             ranked = sorted((r for r in prior if r["n"] == n and r["batch"] == batches[0]), key=lambda r: r["ms"])
             cands = list(dict.fromkeys(r["spec"] for r in ranked))[: a.top] or cands
