@@ -18,33 +18,72 @@ __device__ __forceinline__ uint32_t fdiv(const FastDiv &f, uint32_t x)
 }
 
 // ---------------------------------------------------------------- leaf
-// S x S-word carry-less product by the comb method, in registers: for every
-// bit position j (high to low) of the 32-bit words of b, shift the 2S-word
-// accumulator left by one (funnel shifts) and XOR a into word i of it
-// wherever bit j of b[i] is set (AND with the sign-extended bit: no branch).
-// 32 (S^2 + 4S) integer operations for (32S)^2 bit products.  This replaces
-// the paper's Mult64 (Sec. 2.1, PCLMULQDQ), which the GPU does not have.
-// (Moving the shifts and masks to the FMA pipe with mul.hi/mad.lo measured
-// slower on GB300: mul.hi issues at half rate.)  b is consumed.
+// Mask of bit 8q+7 of x (all ones or all zeros) by byte-sign replication:
+// prmt with selector nibbles 8|q copies the sign of byte q into every byte.
+template <uint32_t Q>
+__device__ __forceinline__ uint32_t byte_sign_mask(uint32_t x)
+{
+    uint32_t d;
+    asm("prmt.b32 %0, %1, 0, %2;" : "=r"(d) : "r"(x), "n"(0x8888u | (Q * 0x1111u)));
+    return d;
+}
+
+// a * X^s as S+1 words (0 < s < 32)
+template <int S>
+__device__ __forceinline__ void shift_words(const uint32_t (&a)[S], uint32_t (&r)[S + 1], uint32_t s)
+{
+    r[0] = a[0] << s;
+#pragma unroll
+    for (int k = 1; k < S; ++k)
+        r[k] = __funnelshift_l(a[k - 1], a[k], s);
+    r[S] = a[S - 1] >> (32u - s);
+}
+
+// S x S-word carry-less product by the comb method, in registers.  Bit
+// 8q+7-u of a word of b contributes a * X^{8q} * X^{7-u}: eight steps u
+// (high to low) shift the 2S-word accumulator left by one (funnel shifts),
+// and in each, every word b[i] gives four masks -- the byte signs of
+// b[i] << u, bits 31-u, 23-u, 15-u, 7-u -- that select a, a X^8, a X^16 and
+// a X^24 (precomputed) into the accumulator at word i (AND with the mask:
+// no branch).  32 S^2 + 83 S + 3 integer operations for (32S)^2 bit
+// products, against 32 S^2 + 128 S for one accumulator shift, one mask and
+// one b shift per bit (measured 3-5% faster on GB300 for S = 4..10).  This
+// replaces the paper's Mult64 (Sec. 2.1, PCLMULQDQ), which the GPU does not
+// have.  (Moving shifts to the FMA pipe with mul.hi measured slower: mul.hi
+// issues at half rate.)  b is consumed.
 template <int S>
 __device__ __forceinline__ void comb(const uint32_t (&a)[S], uint32_t (&b)[S], uint32_t (&c)[2 * S])
 {
+    uint32_t a8[S + 1], a16[S + 1], a24[S + 1];
+    shift_words<S>(a, a8, 8u);
+    shift_words<S>(a, a16, 16u);
+    shift_words<S>(a, a24, 24u);
 #pragma unroll
     for (int i = 0; i < 2 * S; ++i)
         c[i] = 0u;
 #pragma unroll 2
-    for (int j = 0; j < 32; ++j) {
+    for (int u = 0; u < 8; ++u) {
 #pragma unroll
         for (int k = 2 * S - 1; k > 0; --k)
             c[k] = __funnelshift_l(c[k - 1], c[k], 1);
         c[0] <<= 1;
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-            const uint32_t m = (uint32_t)((int32_t)b[i] >> 31);
+            const uint32_t m3 = byte_sign_mask<3>(b[i]), m2 = byte_sign_mask<2>(b[i]);
+            const uint32_t m1 = byte_sign_mask<1>(b[i]), m0 = byte_sign_mask<0>(b[i]);
             b[i] <<= 1;
 #pragma unroll
+            for (int k = 0; k <= S; ++k)
+                c[i + k] ^= a24[k] & m3;
+#pragma unroll
+            for (int k = 0; k <= S; ++k)
+                c[i + k] ^= a16[k] & m2;
+#pragma unroll
+            for (int k = 0; k <= S; ++k)
+                c[i + k] ^= a8[k] & m1;
+#pragma unroll
             for (int k = 0; k < S; ++k)
-                c[i + k] ^= a[k] & m;
+                c[i + k] ^= a[k] & m0;
         }
     }
 }

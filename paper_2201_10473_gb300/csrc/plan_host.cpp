@@ -152,7 +152,9 @@ static void op_model(const GPlan &P, const uint32_t *sz, const uint32_t *npar_al
         }
     }
     const uint64_t S = P.S;
-    const uint64_t leaf = 32 * S * S + 128 * S;                        // comb: S^2 AND-XOR + masks + shifts per bit
+    // comb: 8 steps of (2S accumulator shifts, 4S masks, S b shifts, S(4S+3)
+    // AND-XORs against a, aX^8, aX^16, aX^24) plus 3(S+1) shifts for those copies
+    const uint64_t leaf = 32 * S * S + 83 * S + 3;
     const uint64_t nleaf_total = npar_all[P.nlev];
     *ops_leaf = nleaf_total * leaf;
     *ops_total = ops + *ops_leaf + 2ull * P.L64 * 2;                   // + fold / store
