@@ -215,6 +215,31 @@ gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, co
 gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, size_t count,
                              uint32_t batch_flags, gf2x_stream stream);
 
+/* The products of gf2x_mul_strided with operands and results in HOST memory
+ * (the operation of Sec. 1; the paper's CPU code has no host/device split,
+ * so this call has no counterpart there).  a, b, out: host arrays, same
+ * layout, strides and flags as gf2x_mul_strided; page-locked memory lets
+ * the copies overlap the products (pageable memory works, with copies that
+ * do not overlap).  The batch runs in up to four chunks through two sets of
+ * device buffers owned by the context: while one chunk is multiplied (a
+ * persistent launch on `stream`), the next chunk's operands are copied in
+ * and the previous chunk's results copied out, on two copy streams of the
+ * context ordered by events.
+ *  - Ordering: the first copy waits for all work already enqueued on
+ *    `stream` and for the previous call of this function on the context
+ *    (any stream); `stream` waits for the last result copy, so synchronize
+ *    `stream` before reading `out`.  The caller must not change a or b, nor
+ *    read out, until then.
+ *  - Memory: the device buffers grow to 2 x (chunk products) x (2 stride_in
+ *    + stride_out) limbs on the first call that needs more (cudaMalloc, which
+ *    synchronizes the device) and are kept until gf2x_ctx_destroy.
+ *  - Errors: as gf2x_mul_strided (GF2X_EINVAL for null or overlapping host
+ *    ranges, bad strides or flags); after a GF2X_ECUDA the results are
+ *    undefined. */
+gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b,
+                                  uint32_t n, size_t count, size_t stride_in, size_t stride_out,
+                                  uint32_t flags, gf2x_stream stream);
+
 /* Build and upload (synchronously on `stream`) the current plans of the
  * given sizes, so that later calls and CUDA graph captures find them ready,
  * and make exactly these sizes the ones device-item batches accept (their

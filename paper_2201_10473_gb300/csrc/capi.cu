@@ -40,6 +40,17 @@ struct Staging {
     bool pending = false;
 };
 
+// Device buffers, copy streams and events of gf2x_mul_strided_host: two sets
+// (chunk parity) of a, b and out; in/done/out mark each set's operand copy,
+// product and result copy; last marks the end of the previous call.
+struct HostPipe {
+    uint64_t *buf = nullptr;
+    size_t bytes = 0;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t entry = nullptr, last = nullptr, in[2] = {}, done[2] = {}, out[2] = {};
+    bool ready = false;
+};
+
 }  // namespace
 
 struct gf2x_ctx {
@@ -68,6 +79,7 @@ struct gf2x_ctx {
     cudaEvent_t ws_done = nullptr;                      // recorded after the last split launch
     cudaStream_t ws_stream = nullptr;
     bool ws_used = false;
+    HostPipe hp;                                        // gf2x_mul_strided_host
 };
 
 static std::string plan_key(uint32_t n, const gf2x_plan_spec &spec, int checked)
@@ -195,6 +207,15 @@ extern "C" void gf2x_ctx_destroy(gf2x_ctx *ctx)
         cudaFree(ctx->ws);
     if (ctx->ws_done)
         cudaEventDestroy(ctx->ws_done);
+    HostPipe &hp = ctx->hp;
+    if (hp.buf)
+        cudaFree(hp.buf);
+    for (cudaStream_t st : {hp.h2d, hp.d2h})
+        if (st)
+            cudaStreamDestroy(st);
+    for (cudaEvent_t ev : {hp.entry, hp.last, hp.in[0], hp.in[1], hp.done[0], hp.done[1], hp.out[0], hp.out[1]})
+        if (ev)
+            cudaEventDestroy(ev);
     delete ctx;
 }
 
@@ -613,6 +634,117 @@ extern "C" gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint
         return fail(ctx, GF2X_EINVAL, "batch too large");
     return launch(ctx, args, P.S, P.threads, 4ull * P.smem_words, count,
                   (batch_flags & GF2X_BATCH_PERSISTENT) != 0, s);
+}
+
+static gf2x_status host_pipe_ready(gf2x_ctx *ctx, size_t bytes)
+{
+    HostPipe &hp = ctx->hp;
+    cudaError_t e = cudaSuccess;
+    if (!hp.ready) {
+        e = cudaStreamCreateWithFlags(&hp.h2d, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithFlags(&hp.d2h, cudaStreamNonBlocking);
+        cudaEvent_t *evs[] = {&hp.entry, &hp.last, &hp.in[0], &hp.in[1], &hp.done[0], &hp.done[1], &hp.out[0],
+                              &hp.out[1]};
+        for (cudaEvent_t *ev : evs)
+            if (e == cudaSuccess)
+                e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(hp.last, hp.h2d);   // nothing before the first call
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "host pipeline set-up");
+        hp.ready = true;
+    }
+    if (bytes > hp.bytes) {
+        if (hp.buf) {
+            e = cudaFree(hp.buf);   // synchronizes the device: no copy or product still uses it
+            hp.buf = nullptr;
+            hp.bytes = 0;
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e, "host pipeline buffers");
+        }
+        e = cudaMalloc((void **)&hp.buf, bytes);
+        if (e != cudaSuccess) {
+            hp.buf = nullptr;
+            return e == cudaErrorMemoryAllocation ? fail(ctx, GF2X_ENOMEM, "host pipeline buffers")
+                                                  : cuda_fail(ctx, e, "host pipeline buffers");
+        }
+        hp.bytes = bytes;
+    }
+    return GF2X_OK;
+}
+
+extern "C" gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b,
+                                             uint32_t n, size_t count, size_t stride_in, size_t stride_out,
+                                             uint32_t flags, gf2x_stream stream)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    if (count == 0)
+        return GF2X_OK;
+    if (n < 1 || n > GF2X_MAX_N)
+        return fail(ctx, GF2X_EUNSUPPORTED, "n outside [1, 131072]");
+    gf2x_status st = check_operands(ctx, out, a, b, n, flags, count, stride_in, stride_out);
+    if (st != GF2X_OK)
+        return st;
+    const size_t L = (n + 63) / 64;
+    const size_t Lo = (flags & GF2X_REDUCE) ? L : (size_t)((2ull * n - 1 + 63) / 64);
+    const size_t si = count > 1 ? stride_in : L, so = count > 1 ? stride_out : Lo;   // device strides
+    const size_t nchunk = count >= 2048 ? 4 : (count >= 512 ? 2 : 1);
+    const size_t K = (count + nchunk - 1) / nchunk;
+    const size_t in_w = K * si, set_w = 2 * in_w + K * so;
+    st = host_pipe_ready(ctx, 2 * set_w * sizeof(uint64_t));
+    if (st != GF2X_OK)
+        return st;
+    HostPipe &hp = ctx->hp;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaEventRecord(hp.entry, s);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(hp.h2d, hp.entry, 0);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(hp.h2d, hp.last, 0);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "host pipeline ordering");
+    for (size_t c = 0, c0 = 0; c0 < count; ++c, c0 += K) {
+        const int p = (int)(c & 1);
+        const size_t k = std::min(K, count - c0);
+        uint64_t *da = hp.buf + p * set_w, *db = da + in_w, *dout = db + in_w;
+        const size_t in_bytes = 8 * ((k - 1) * si + L), out_bytes = 8 * ((k - 1) * so + Lo);
+        if (c >= 2)   // the set's previous product has read its operands
+            e = cudaStreamWaitEvent(hp.h2d, hp.done[p], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(da, a + c0 * si, in_bytes, cudaMemcpyHostToDevice, hp.h2d);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(db, b + c0 * si, in_bytes, cudaMemcpyHostToDevice, hp.h2d);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(hp.in[p], hp.h2d);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(s, hp.in[p], 0);
+        if (e == cudaSuccess && c >= 2)   // the set's previous results have been copied out
+            e = cudaStreamWaitEvent(s, hp.out[p], 0);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "host pipeline copy in");
+        st = gf2x_mul_strided(ctx, dout, da, db, n, k, si, so, flags, GF2X_BATCH_PERSISTENT, stream);
+        if (st != GF2X_OK)
+            return st;
+        e = cudaEventRecord(hp.done[p], s);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(hp.d2h, hp.done[p], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out + c0 * so, dout, out_bytes, cudaMemcpyDeviceToHost, hp.d2h);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(hp.out[p], hp.d2h);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "host pipeline copy out");
+    }
+    e = cudaStreamWaitEvent(s, hp.out[0], 0);
+    if (e == cudaSuccess && nchunk > 1)
+        e = cudaStreamWaitEvent(s, hp.out[1], 0);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(hp.last, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "host pipeline completion");
+    return GF2X_OK;
 }
 
 // Take a staging buffer of at least `count` items; waits (host) for the

@@ -77,6 +77,7 @@ _SIGNATURES = {
     "gf2x_mul": ([_P, _P, _P, _P, _U32, _P], _I),
     "gf2x_mulmod_xn1": ([_P, _P, _P, _P, _U32, _P], _I),
     "gf2x_mul_strided": ([_P, _P, _P, _P, _U32, _SZ, _SZ, _SZ, _U32, _U32, _P], _I),
+    "gf2x_mul_strided_host": ([_P, _P, _P, _P, _U32, _SZ, _SZ, _SZ, _U32, _P], _I),
     "gf2x_mul_batched": ([_P, _P, _SZ, _U32, _P], _I),
     "gf2x_ctx_prepare": ([_P, ctypes.POINTER(_U32), _SZ, _P], _I),
     "gf2x_ctx_launch_shape": ([_P, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32),
@@ -274,6 +275,31 @@ class Context:
                                            a.shape[1], out.shape[1], REDUCE if reduce else 0,
                                            BATCH_PERSISTENT if persistent else 0, _stream_handle(stream)),
                     "gf2x_mul_strided")
+        return out
+
+    def mul_strided_host(self, a: torch.Tensor, b: torch.Tensor, n: int, reduce: bool,
+                         out: torch.Tensor | None = None, stream=None):
+        """mul_strided with CPU tensors (pinned for overlapped copies): the
+        library copies chunks in, multiplies and copies results out on its own
+        streams; `stream` waits for the last copy.  Keep a, b and out alive and
+        unchanged until `stream` has been synchronized."""
+        if a.dim() != 2 or a.shape != b.shape:
+            raise ValueError("a and b must be equal-shaped 2-D tensors")
+        for t, name in ((a, "a"), (b, "b")):
+            if t.device.type != "cpu" or t.dtype != torch.int64 or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous int64 CPU tensor")
+            if t.shape[1] < limbs(n):
+                raise ValueError(f"{name} has fewer than ceil(n/64) limbs")
+        count = a.shape[0]
+        ol = limbs(n) if reduce else full_limbs(n)
+        if out is None:
+            out = torch.empty((count, ol), dtype=torch.int64, pin_memory=True)
+        if out.device.type != "cpu" or out.dim() != 2 or out.shape[0] != count or out.shape[1] < ol \
+                or not out.is_contiguous():
+            raise ValueError("bad output tensor")
+        self._raise(lib().gf2x_mul_strided_host(self._h, out.data_ptr(), a.data_ptr(), b.data_ptr(), n, count,
+                                                a.shape[1], out.shape[1], REDUCE if reduce else 0,
+                                                _stream_handle(stream)), "gf2x_mul_strided_host")
         return out
 
     def mul_batched(self, items, persistent: bool = False, largest_first: bool = False, stream=None):
