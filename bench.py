@@ -339,7 +339,7 @@ def run_ours(args, w):
 
     def e2e_step():
         # the public host-buffer call: chunked copies in and out overlapped with the products
-        ctx.mul_strided_host(pin_a, pin_b, n, reduce, out=pin_out, stream=stream)
+        ctx.mul_strided_host(pin_a, pin_b, n, reduce, out=pin_out, stream=stream, inputs_ready=True)
 
     for _ in range(2):
         e2e_step()

@@ -225,17 +225,22 @@ gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, size_t count
  * persistent launch on `stream`), the next chunk's operands are copied in
  * and the previous chunk's results copied out, on two copy streams of the
  * context ordered by events.
- *  - Ordering: the first copy waits for all work already enqueued on
- *    `stream` and for the previous call of this function on the context
- *    (any stream); `stream` waits for the last result copy, so synchronize
- *    `stream` before reading `out`.  The caller must not change a or b, nor
- *    read out, until then.
+ *  - Ordering: the products wait for all work already enqueued on
+ *    `stream`, and so do the operand copies unless flags has
+ *    GF2X_HOST_INPUTS_READY (a and b are final at the call: their copies may
+ *    then overlap earlier work, e.g. the previous call's last products).  A
+ *    device buffer set is reused only after its previous product and result
+ *    copy, whichever call (and stream) made them.  `stream` waits for the
+ *    last result copy: synchronize it before reading `out`; the caller must
+ *    not change a or b, nor read out, until then.
  *  - Memory: the device buffers grow to 2 x (chunk products) x (2 stride_in
  *    + stride_out) limbs on the first call that needs more (cudaMalloc, which
  *    synchronizes the device) and are kept until gf2x_ctx_destroy.
  *  - Errors: as gf2x_mul_strided (GF2X_EINVAL for null or overlapping host
  *    ranges, bad strides or flags); after a GF2X_ECUDA the results are
  *    undefined. */
+#define GF2X_HOST_INPUTS_READY (1u << 8)
+
 gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b,
                                   uint32_t n, size_t count, size_t stride_in, size_t stride_out,
                                   uint32_t flags, gf2x_stream stream);

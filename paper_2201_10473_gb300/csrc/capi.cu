@@ -41,13 +41,14 @@ struct Staging {
 };
 
 // Device buffers, copy streams and events of gf2x_mul_strided_host: two sets
-// (chunk parity) of a, b and out; in/done/out mark each set's operand copy,
-// product and result copy; last marks the end of the previous call.
+// (chunk parity) of a, b and out; in/done/out mark each set's last operand
+// copy, product and result copy (across calls: a set is reused only after
+// its previous product and result copy, whichever call made them).
 struct HostPipe {
     uint64_t *buf = nullptr;
     size_t bytes = 0;
     cudaStream_t h2d = nullptr, d2h = nullptr;
-    cudaEvent_t entry = nullptr, last = nullptr, in[2] = {}, done[2] = {}, out[2] = {};
+    cudaEvent_t entry = nullptr, in[2] = {}, done[2] = {}, out[2] = {};
     bool ready = false;
 };
 
@@ -213,7 +214,7 @@ extern "C" void gf2x_ctx_destroy(gf2x_ctx *ctx)
     for (cudaStream_t st : {hp.h2d, hp.d2h})
         if (st)
             cudaStreamDestroy(st);
-    for (cudaEvent_t ev : {hp.entry, hp.last, hp.in[0], hp.in[1], hp.done[0], hp.done[1], hp.out[0], hp.out[1]})
+    for (cudaEvent_t ev : {hp.entry, hp.in[0], hp.in[1], hp.done[0], hp.done[1], hp.out[0], hp.out[1]})
         if (ev)
             cudaEventDestroy(ev);
     delete ctx;
@@ -644,13 +645,10 @@ static gf2x_status host_pipe_ready(gf2x_ctx *ctx, size_t bytes)
         e = cudaStreamCreateWithFlags(&hp.h2d, cudaStreamNonBlocking);
         if (e == cudaSuccess)
             e = cudaStreamCreateWithFlags(&hp.d2h, cudaStreamNonBlocking);
-        cudaEvent_t *evs[] = {&hp.entry, &hp.last, &hp.in[0], &hp.in[1], &hp.done[0], &hp.done[1], &hp.out[0],
-                              &hp.out[1]};
+        cudaEvent_t *evs[] = {&hp.entry, &hp.in[0], &hp.in[1], &hp.done[0], &hp.done[1], &hp.out[0], &hp.out[1]};
         for (cudaEvent_t *ev : evs)
             if (e == cudaSuccess)
                 e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
-        if (e == cudaSuccess)
-            e = cudaEventRecord(hp.last, hp.h2d);   // nothing before the first call
         if (e != cudaSuccess)
             return cuda_fail(ctx, e, "host pipeline set-up");
         hp.ready = true;
@@ -684,6 +682,8 @@ extern "C" gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const
         return GF2X_OK;
     if (n < 1 || n > GF2X_MAX_N)
         return fail(ctx, GF2X_EUNSUPPORTED, "n outside [1, 131072]");
+    const bool inputs_ready = (flags & GF2X_HOST_INPUTS_READY) != 0;
+    flags &= ~(uint32_t)GF2X_HOST_INPUTS_READY;
     gf2x_status st = check_operands(ctx, out, a, b, n, flags, count, stride_in, stride_out);
     if (st != GF2X_OK)
         return st;
@@ -698,20 +698,21 @@ extern "C" gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const
         return st;
     HostPipe &hp = ctx->hp;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaEventRecord(hp.entry, s);
-    if (e == cudaSuccess)
-        e = cudaStreamWaitEvent(hp.h2d, hp.entry, 0);
-    if (e == cudaSuccess)
-        e = cudaStreamWaitEvent(hp.h2d, hp.last, 0);
-    if (e != cudaSuccess)
-        return cuda_fail(ctx, e, "host pipeline ordering");
+    cudaError_t e = cudaSuccess;
+    if (!inputs_ready) {   // the operand copies wait for the work already on `stream`
+        e = cudaEventRecord(hp.entry, s);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(hp.h2d, hp.entry, 0);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "host pipeline ordering");
+    }
     for (size_t c = 0, c0 = 0; c0 < count; ++c, c0 += K) {
         const int p = (int)(c & 1);
         const size_t k = std::min(K, count - c0);
         uint64_t *da = hp.buf + p * set_w, *db = da + in_w, *dout = db + in_w;
         const size_t in_bytes = 8 * ((k - 1) * si + L), out_bytes = 8 * ((k - 1) * so + Lo);
-        if (c >= 2)   // the set's previous product has read its operands
-            e = cudaStreamWaitEvent(hp.h2d, hp.done[p], 0);
+        // the set's previous product (this call or an earlier one) has read its operands
+        e = cudaStreamWaitEvent(hp.h2d, hp.done[p], 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(da, a + c0 * si, in_bytes, cudaMemcpyHostToDevice, hp.h2d);
         if (e == cudaSuccess)
@@ -720,7 +721,7 @@ extern "C" gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const
             e = cudaEventRecord(hp.in[p], hp.h2d);
         if (e == cudaSuccess)
             e = cudaStreamWaitEvent(s, hp.in[p], 0);
-        if (e == cudaSuccess && c >= 2)   // the set's previous results have been copied out
+        if (e == cudaSuccess)   // the set's previous results have been copied out
             e = cudaStreamWaitEvent(s, hp.out[p], 0);
         if (e != cudaSuccess)
             return cuda_fail(ctx, e, "host pipeline copy in");
@@ -740,8 +741,6 @@ extern "C" gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const
     e = cudaStreamWaitEvent(s, hp.out[0], 0);
     if (e == cudaSuccess && nchunk > 1)
         e = cudaStreamWaitEvent(s, hp.out[1], 0);
-    if (e == cudaSuccess)
-        e = cudaEventRecord(hp.last, s);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "host pipeline completion");
     return GF2X_OK;

@@ -23,6 +23,7 @@ MAX_LEVELS = 8
 LEVEL_KARATSUBA = 0
 LEVEL_TOOM3 = 1
 REDUCE = 1
+HOST_INPUTS_READY = 1 << 8
 BATCH_PERSISTENT = 1
 BATCH_ITEMS_ON_DEVICE = 2
 BATCH_LARGEST_FIRST = 4
@@ -278,11 +279,13 @@ class Context:
         return out
 
     def mul_strided_host(self, a: torch.Tensor, b: torch.Tensor, n: int, reduce: bool,
-                         out: torch.Tensor | None = None, stream=None):
+                         out: torch.Tensor | None = None, stream=None, inputs_ready: bool = False):
         """mul_strided with CPU tensors (pinned for overlapped copies): the
         library copies chunks in, multiplies and copies results out on its own
         streams; `stream` waits for the last copy.  Keep a, b and out alive and
-        unchanged until `stream` has been synchronized."""
+        unchanged until `stream` has been synchronized.  inputs_ready: a and b
+        are final now, so their copies need not wait for earlier work on
+        `stream`."""
         if a.dim() != 2 or a.shape != b.shape:
             raise ValueError("a and b must be equal-shaped 2-D tensors")
         for t, name in ((a, "a"), (b, "b")):
@@ -298,7 +301,8 @@ class Context:
                 or not out.is_contiguous():
             raise ValueError("bad output tensor")
         self._raise(lib().gf2x_mul_strided_host(self._h, out.data_ptr(), a.data_ptr(), b.data_ptr(), n, count,
-                                                a.shape[1], out.shape[1], REDUCE if reduce else 0,
+                                                a.shape[1], out.shape[1],
+                                                (REDUCE if reduce else 0) | (HOST_INPUTS_READY if inputs_ready else 0),
                                                 _stream_handle(stream)), "gf2x_mul_strided_host")
         return out
 

@@ -47,17 +47,18 @@ def test_host_entry_matches_device_entry(n, count, reduce, spec, pinned):
         ctx.close()
 
 
-def test_calls_in_a_row_on_two_streams_keep_their_own_results():
+@pytest.mark.parametrize("ready", [False, True])
+def test_calls_in_a_row_on_two_streams_keep_their_own_results(ready):
     from paper_2201_10473_gb300 import Context
     n, count = 17669, 2500
     ctx = Context(0)
     try:
         s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
-        ins = [wl.dense_pair(9300 + k, n, count) for k in range(3)]
+        ins = [wl.dense_pair(9300 + k, n, count) for k in range(5)]
         hosts = [(_host(a, True), _host(b, True)) for a, b in ins]     # alive until the copies have run
         outs = []
         for k, (ha, hb) in enumerate(hosts):     # no synchronization between the calls
-            outs.append(ctx.mul_strided_host(ha, hb, n, True, stream=(s1, s2)[k % 2]))
+            outs.append(ctx.mul_strided_host(ha, hb, n, True, stream=(s1, s1, s2, s1, s2)[k], inputs_ready=ready))
         s1.synchronize()
         s2.synchronize()
         for (a, b), got in zip(ins, outs):
