@@ -629,6 +629,7 @@ fused_mul_kernel(const LaunchArgs args)
     __shared__ GPlan P;
     const uint32_t smem_avail = dynamic_smem_bytes();
     const uint32_t step = args.persistent ? gridDim.x : args.count;
+    uint32_t loaded = kEmptyItem;   // plan slot currently in P (none)
     for (uint32_t i = blockIdx.x; i < args.count; i += step) {
         const DevItem it = fetch_item(args, i);
         if (it.plan >= kEmptyItem) {  // uniform over the CTA: every thread read the same item
@@ -636,14 +637,15 @@ fused_mul_kernel(const LaunchArgs args)
                 flag_error(args.err, kErrNoPlan);
             continue;
         }
-        __syncthreads();
-        {
+        __syncthreads();   // the previous product is done with shared memory
+        if (it.plan != loaded) {   // uniform: a persistent CTA of a uniform batch loads its plan once
             const uint32_t *src = reinterpret_cast<const uint32_t *>(args.plans + it.plan);
             uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
             for (uint32_t w = threadIdx.x; w < sizeof(GPlan) / 4; w += blockDim.x)
                 dst[w] = __ldg(src + w);
+            loaded = it.plan;
+            __syncthreads();
         }
-        __syncthreads();
         // a plan made for another leaf size or more shared memory than this
         // launch has is refused (uniform over the CTA), never run
         if (P.S != (uint32_t)S || 4u * P.smem_words > smem_avail || P.nlev > (uint32_t)kMaxLevels) {
