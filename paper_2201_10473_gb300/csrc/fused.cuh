@@ -293,6 +293,85 @@ __device__ __forceinline__ void interp_k2(const GLevel &L, const uint32_t *__res
     }
 }
 
+// Two 2-way Karatsuba levels in one pass (Alg. 1 applied twice): parent
+// operands of 4G words (quarters q0..q3) give the nine grandchildren
+// (j1, j2), child j1 = (q0 q1), (q2 q3) or (q0+q2, q1+q3) and grandchild j2
+// its low half, high half or their sum -- each grandchild word the XOR of 1,
+// 2 or 4 quarter words at one offset.  Two words per thread.
+__device__ __forceinline__ void eval_k2x2(const GLevel &L1, const GLevel &L2, const uint32_t *__restrict__ par,
+                                          uint32_t *__restrict__ ch, uint32_t npar)
+{
+    const uint32_t G = L2.E, T = L1.T;   // T = 4G
+    const uint32_t total = npar * (G / 2u);
+    for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const uint32_t p = fdiv(L2.divhE, idx);
+        const uint32_t e = 2u * idx - p * G;
+        const uint32_t *X = par + p * (2u * T);
+        uint32_t *C = ch + p * (18u * G);
+#pragma unroll
+        for (uint32_t op = 0; op < 2; ++op) {   // A, then B
+            const uint32_t *Q = X + op * T;
+            const uint2 q0 = *reinterpret_cast<const uint2 *>(Q + e);
+            const uint2 q1 = *reinterpret_cast<const uint2 *>(Q + G + e);
+            const uint2 q2 = *reinterpret_cast<const uint2 *>(Q + 2u * G + e);
+            const uint2 q3 = *reinterpret_cast<const uint2 *>(Q + 3u * G + e);
+            const uint2 q01 = make_uint2(q0.x ^ q1.x, q0.y ^ q1.y), q23 = make_uint2(q2.x ^ q3.x, q2.y ^ q3.y);
+            const uint2 q02 = make_uint2(q0.x ^ q2.x, q0.y ^ q2.y), q13 = make_uint2(q1.x ^ q3.x, q1.y ^ q3.y);
+            const uint2 v[9] = {q0, q1, q01, q2, q3, q23, q02, q13, make_uint2(q01.x ^ q23.x, q01.y ^ q23.y)};
+            uint32_t *D = C + op * G + e;
+#pragma unroll
+            for (uint32_t g = 0; g < 9; ++g)
+                *reinterpret_cast<uint2 *>(D + g * (2u * G)) = v[g];
+        }
+    }
+}
+
+// The reconstruction of such a pair: with Q the grandchild products (2G
+// words, blocks of G), child j is R = Q0 + X^G (Q0+Q1+Q2) + X^2G Q1 and the
+// parent P = R0 + X^2G (R0+R1+R2) + X^4G R1, eight blocks of G words per
+// offset in registers.
+__device__ __forceinline__ void interp_k2x2(const GLevel &L1, const GLevel &L2, const uint32_t *__restrict__ ch,
+                                            uint32_t *__restrict__ par, uint32_t npar)
+{
+    const uint32_t G = L2.E, T = L1.T;
+    const uint32_t total = npar * (G / 2u);
+    for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const uint32_t p = fdiv(L2.divhE, idx);
+        const uint32_t e = 2u * idx - p * G;
+        const uint32_t *Q = ch + p * (18u * G) + e;
+        uint2 R[3][4];
+#pragma unroll
+        for (uint32_t j = 0; j < 3; ++j) {
+            const uint32_t *q = Q + j * (6u * G);
+            const uint2 a0 = *reinterpret_cast<const uint2 *>(q);
+            const uint2 a1 = *reinterpret_cast<const uint2 *>(q + G);
+            const uint2 b0 = *reinterpret_cast<const uint2 *>(q + 2u * G);
+            const uint2 b1 = *reinterpret_cast<const uint2 *>(q + 3u * G);
+            const uint2 c0 = *reinterpret_cast<const uint2 *>(q + 4u * G);
+            const uint2 c1 = *reinterpret_cast<const uint2 *>(q + 5u * G);
+            const uint2 m0 = make_uint2(a0.x ^ b0.x ^ c0.x, a0.y ^ b0.y ^ c0.y);
+            const uint2 m1 = make_uint2(a1.x ^ b1.x ^ c1.x, a1.y ^ b1.y ^ c1.y);
+            R[j][0] = a0;
+            R[j][1] = make_uint2(a1.x ^ m0.x, a1.y ^ m0.y);
+            R[j][2] = make_uint2(m1.x ^ b0.x, m1.y ^ b0.y);
+            R[j][3] = b1;
+        }
+        uint32_t *C = par + p * (2u * T) + e;
+#pragma unroll
+        for (uint32_t b = 0; b < 8; ++b) {
+            uint2 v = make_uint2(0u, 0u);
+            if (b < 4)
+                v = R[0][b];
+            if (b >= 2 && b < 6)
+                v = make_uint2(v.x ^ R[0][b - 2].x ^ R[1][b - 2].x ^ R[2][b - 2].x,
+                               v.y ^ R[0][b - 2].y ^ R[1][b - 2].y ^ R[2][b - 2].y);
+            if (b >= 4)
+                v = make_uint2(v.x ^ R[1][b - 4].x, v.y ^ R[1][b - 4].y);
+            *reinterpret_cast<uint2 *>(C + b * G) = v;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- interpolation
 // k-way Karatsuba reconstruction: word q of the parent product is the XOR of
 // term_p[q - pE] for the (at most two) positions p covering q.
@@ -535,6 +614,32 @@ __device__ __forceinline__ void eval_pass(const GLevel &L, const uint32_t *par, 
         eval_level(L, par, ch, c_begin, c_count);
 }
 
+// One level's evaluation pass (a pair's first level runs both; its second none).
+__device__ __forceinline__ void eval_step(const GPlan &P, uint32_t l, uint32_t *sm)
+{
+    const GLevel &L = P.lev[l];
+    if (L.pair == 2u)
+        return;
+    if (L.pair == 1u)
+        eval_k2x2(L, P.lev[l + 1], sm + L.in_off, sm + L.ch_off, L.npar);
+    else
+        eval_pass(L, sm + L.in_off, sm + L.ch_off, 0u, L.npar * L.nch, L.npar);
+    __syncthreads();
+}
+
+__device__ __forceinline__ void interp_step(const GPlan &P, uint32_t l, uint32_t *sm, uint32_t *err)
+{
+    const GLevel &L = P.lev[l];
+    if (L.pair == 2u)
+        return;
+    if (L.pair == 1u) {
+        interp_k2x2(L, P.lev[l + 1], sm + L.ch_off, sm + L.in_off, L.npar);
+        __syncthreads();
+    } else {
+        interp_level(P, L, sm + L.ch_off, sm + L.in_off, sm, L.npar, err);
+    }
+}
+
 template <int S>
 __device__ void run_product(const GPlan &P, const DevItem &it, uint32_t *sm, uint32_t *err)
 {
@@ -551,34 +656,24 @@ __device__ void run_product(const GPlan &P, const DevItem &it, uint32_t *sm, uin
     } else {
         uint32_t *leaf_base = sm + (P.fuse_k2 ? P.lev[nlev - 1].in_off : P.lev[nlev - 1].ch_off);
         if (!P.seq_top) {
-            for (uint32_t l = 0; l < ne; ++l) {
-                const GLevel &L = P.lev[l];
-                eval_pass(L, sm + L.in_off, sm + L.ch_off, 0u, L.npar * L.nch, L.npar);
-                __syncthreads();
-            }
+            for (uint32_t l = 0; l < ne; ++l)
+                eval_step(P, l, sm);
             leaf_pass<S>(P, leaf_base, P.nleaf_pass);
             __syncthreads();
-            for (int l = (int)ne - 1; l >= 0; --l) {
-                const GLevel &L = P.lev[l];
-                interp_level(P, L, sm + L.ch_off, sm + L.in_off, sm, L.npar, err);
-            }
+            for (int l = (int)ne - 1; l >= 0; --l)
+                interp_step(P, (uint32_t)l, sm, err);
         } else {
             const GLevel &L0 = P.lev[0];
             const uint32_t twoE0 = 2u * L0.E;
             for (uint32_t j = 0; j < L0.nch; ++j) {
                 eval_level(L0, sm + L0.in_off, sm + L0.ch_off, j, 1u);
                 __syncthreads();
-                for (uint32_t l = 1; l < ne; ++l) {
-                    const GLevel &L = P.lev[l];
-                    eval_pass(L, sm + L.in_off, sm + L.ch_off, 0u, L.npar * L.nch, L.npar);
-                    __syncthreads();
-                }
+                for (uint32_t l = 1; l < ne; ++l)
+                    eval_step(P, l, sm);
                 leaf_pass<S>(P, leaf_base, P.nleaf_pass);
                 __syncthreads();
-                for (int l = (int)ne - 1; l >= 1; --l) {
-                    const GLevel &L = P.lev[l];
-                    interp_level(P, L, sm + L.ch_off, sm + L.in_off, sm, L.npar, err);
-                }
+                for (int l = (int)ne - 1; l >= 1; --l)
+                    interp_step(P, (uint32_t)l, sm, err);
                 const uint32_t *src = sm + L0.ch_off;
                 uint32_t *dst = sm + P.prod_off + j * twoE0;
                 for (uint32_t w = threadIdx.x; w < twoE0; w += blockDim.x)

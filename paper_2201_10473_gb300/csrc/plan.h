@@ -43,7 +43,9 @@ struct GLevel {
     uint8_t sel[16][2];                 // Karatsuba child j = X[sel0] ^ X[sel1] (sel1 = 255: single)
     uint8_t nterms[2 * 5 - 1];
     uint8_t terms[2 * 5 - 1][kMaxTerms];  // children XORed into reconstruction term p
-    uint8_t pad_[3];
+    uint8_t pair;       // 1: this 2-way level and the next run as one pass (9 grandchildren);
+                        // 2: the second level of such a pair (no pass of its own)
+    uint8_t pad_[2];
 };
 
 struct GPlan {

@@ -269,27 +269,57 @@ gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec_in, GPlan *out, gf
         L.divhE = make_div(std::max(1u, L.E / 2));
     }
 
+    // ---- fused pairs of 2-way levels: levels l, l+1 (both K2, both shared-
+    // memory passes, not the per-child top of seq_top) run as one pass from
+    // depth l to depth l+2; depth l+1 is never stored.  Paired from the leaf
+    // side upwards.
+    const uint32_t ne = s.nlev - s.fuse_leaf;   // levels run as shared-memory passes
+    bool mat[kMaxLevels + 1];
+    for (uint32_t d = 0; d <= s.nlev; ++d)
+        mat[d] = true;
+    for (int l = (int)ne - 2; l >= (s.seq_top ? 1 : 0); --l) {
+        GLevel &A = P.lev[l], &B = P.lev[l + 1];
+        if (A.pair || B.pair || A.kind != kKaratsuba || B.kind != kKaratsuba || A.k != 2 || B.k != 2 || (B.E & 1u))
+            continue;
+        A.pair = 1;
+        B.pair = 2;
+        mat[l + 1] = false;
+        --l;   // the level above this pair may pair with the one above it
+    }
+
     // ---- shared-memory layout (words, 16-byte aligned regions)
-    // data at depth d: npar_pass[d] slots of 2*sz[d] words
+    // data at depth d: npar_pass[d] slots of 2*sz[d] words; stored depths
+    // alternate between two regions
     uint32_t D[kMaxLevels + 1];
     for (uint32_t d = 0; d <= s.nlev; ++d)
-        D[d] = d <= deepest ? round_up(npar_pass[d] * 2 * sz[d], 4) : 0;
+        D[d] = (d <= deepest && mat[d]) ? round_up(npar_pass[d] * 2 * sz[d], 4) : 0;
+    uint32_t par_of[kMaxLevels + 1];   // region parity of every stored depth
+    {
+        uint32_t k = 0;
+        for (uint32_t d = 0; d <= s.nlev; ++d)
+            par_of[d] = mat[d] ? (k++ & 1u) : 0u;
+    }
+    // the depth a level's pass writes: l+1, or l+2 for the first of a pair
+    auto out_depth = [&](uint32_t l) { return P.lev[l].pair == 1 ? l + 2 : l + 1; };
     uint32_t off = 0;
     uint32_t regA = 0, regB = 0, regP = 0;
     if (!s.seq_top) {
         for (uint32_t d = 0; d <= s.nlev; ++d)
-            (d % 2 == 0 ? regA : regB) = std::max(d % 2 == 0 ? regA : regB, D[d]);
+            (par_of[d] == 0 ? regA : regB) = std::max(par_of[d] == 0 ? regA : regB, D[d]);
         uint32_t offA = off;
         off += regA;
         uint32_t offB = off;
         off += regB;
         P.top_off = offA;
         for (uint32_t l = 0; l < s.nlev; ++l) {
-            P.lev[l].in_off = (l % 2 == 0) ? offA : offB;
-            P.lev[l].ch_off = (l % 2 == 0) ? offB : offA;
+            const uint32_t din = P.lev[l].pair == 2 ? l - 1 : l;
+            const uint32_t dout = P.lev[l].pair == 2 ? l + 1 : out_depth(l);
+            P.lev[l].in_off = par_of[din] == 0 ? offA : offB;
+            P.lev[l].ch_off = par_of[dout] == 0 ? offA : offB;
         }
     } else {
-        // top slot, children products, then ping-pong Y (odd depth) / Z (even depth >= 2)
+        // top slot, children products, then two regions Y / Z alternating over
+        // the stored depths >= 1 (depth 1 in Y)
         uint32_t offX = off;
         off += D[0];
         regP = round_up(P.lev[0].nch * 2 * sz[1], 4);
@@ -297,17 +327,20 @@ gf2x_status build_plan(uint32_t n, const gf2x_plan_spec *spec_in, GPlan *out, gf
         off += regP;
         uint32_t regY = 0, regZ = 0;
         for (uint32_t d = 1; d <= s.nlev; ++d)
-            (d % 2 == 1 ? regY : regZ) = std::max(d % 2 == 1 ? regY : regZ, D[d]);
+            (par_of[d] == par_of[1] ? regY : regZ) = std::max(par_of[d] == par_of[1] ? regY : regZ, D[d]);
         uint32_t offY = off;
         off += regY;
         uint32_t offZ = off;
         off += regZ;
+        auto region = [&](uint32_t d) { return par_of[d] == par_of[1] ? offY : offZ; };
         P.top_off = offX;
         P.lev[0].in_off = offX;
         P.lev[0].ch_off = offY;
         for (uint32_t l = 1; l < s.nlev; ++l) {
-            P.lev[l].in_off = (l % 2 == 1) ? offY : offZ;
-            P.lev[l].ch_off = (l % 2 == 1) ? offZ : offY;
+            const uint32_t din = P.lev[l].pair == 2 ? l - 1 : l;
+            const uint32_t dout = P.lev[l].pair == 2 ? l + 1 : out_depth(l);
+            P.lev[l].in_off = region(din);
+            P.lev[l].ch_off = region(dout);
         }
     }
     // Toom-3 temporaries: two arrays of 2E words per parent (c3 and the c2 numerator)
