@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle cpu_baseline sample")
     p.add_argument("--no-extras", action="store_true", help="skip the other workloads (C1, C3, C4, C5)")
     p.add_argument("--serving-requests", type=int, default=200000)
+    p.add_argument("--plan", default=None, help="plan spec for the main workload (default: the tuned database)")
     return p.parse_args()
 
 
@@ -266,6 +267,8 @@ def run_ours(args, w):
     n, batch, reduce = w["n"], w["batch"], w["reduce"]
     seed = wl.BASE_SEED + w["key"]
     ctx = Context(local, batch_hint=batch)
+    if args.plan:
+        ctx.set_plan(n, args.plan)
     spec = ctx.get_plan(n)
     info = plan_info(n, spec)
     shape = ctx.launch_shape(n)

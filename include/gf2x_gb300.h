@@ -155,7 +155,9 @@ gf2x_status gf2x_ctx_create(gf2x_ctx **ctx, int device);
 void gf2x_ctx_destroy(gf2x_ctx *ctx);
 
 /* Use `spec` for every later product of size n in this context
- * (spec = NULL restores the default).  Host-side validation only. */
+ * (spec = NULL restores the default).  Host-side validation only.  On an
+ * error (a spec that does not fit n, or GF2X_EUNSUPPORTED "plan table full"
+ * after 8192 distinct plans in one context) the previous plan stays in force. */
 gf2x_status gf2x_ctx_set_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_plan_spec *spec);
 
 /* Load a plan database written by the autotuner: text lines

@@ -105,6 +105,13 @@ class Autotuner:
         self.reps = reps
         self.warmup = warmup
         self._inputs = {}
+        self.failures = []   # (n, batch, spec, message) of candidates that could not be measured
+
+    def renew_context(self):
+        """Replace the context by a fresh one on the same device (same plan database)."""
+        old = self.ctx
+        self.ctx = gf2x.Context(old.device, plan_db=getattr(old, "plan_db", "packaged"))
+        old.close()
 
     def _operands(self, n: int, batch: int):
         key = (n, batch)
@@ -173,7 +180,15 @@ class Autotuner:
                 break
             try:
                 res.append(self.measure(n, s, batch))
-            except gf2x.Gf2xError:
+            except gf2x.Gf2xError as e:
+                if "plan table full" in str(e):   # a context holds 8192 plans: go on in a fresh one
+                    self.renew_context()
+                    try:
+                        res.append(self.measure(n, s, batch))
+                        continue
+                    except gf2x.Gf2xError as e2:
+                        e = e2
+                self.failures.append((n, batch, s, str(e)))
                 continue
         res.sort(key=lambda m: m.ms)
         return res
@@ -334,7 +349,7 @@ def main(argv=None):
         res = tuner.search(n, batches[0], cands, a.budget)
         if not res:
             print(f"n={n}: no candidate could be measured", flush=True)
-            ctx.close()
+            tuner.ctx.close()
             continue
         record_best(db, n, batches[0], res[0])
         print(f"n={n} batch={batches[0]} measured={len(res)} best={res[0].spec} {res[0].mults_per_s:.4g}/s "
@@ -342,10 +357,15 @@ def main(argv=None):
         for bsz in batches[1:]:
             sub = [m.spec for m in res[:20]] + rng.sample(cands, min(a.sample, len(cands)))
             r2 = tuner.search(n, bsz, list(dict.fromkeys(sub)), a.budget)
+            if not r2:
+                print(f"n={n} batch={bsz}: no candidate could be measured", flush=True)
+                continue
             record_best(db, n, bsz, r2[0])
             print(f"n={n} batch={bsz} measured={len(r2)} best={r2[0].spec} {r2[0].mults_per_s:.4g}/s", flush=True)
+        if tuner.failures:
+            print(f"n={n}: {len(tuner.failures)} candidates failed, first: {tuner.failures[0]}", flush=True)
         save_db(a.db, db, header="tuned on " + torch_device_name())
-        ctx.close()
+        tuner.ctx.close()
 
 
 def torch_device_name() -> str:

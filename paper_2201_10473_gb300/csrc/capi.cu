@@ -305,9 +305,9 @@ extern "C" gf2x_status gf2x_ctx_set_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_p
     if (n < 1 || n > GF2X_MAX_N)
         return fail(ctx, GF2X_EUNSUPPORTED, "n outside [1, 131072]");
     cudaSetDevice(ctx->device);
-    ctx->by_n.erase(n);
-    ctx->by_n_checked.erase(n);
     if (!spec) {
+        ctx->by_n.erase(n);
+        ctx->by_n_checked.erase(n);
         if (in_device_set(ctx, n)) {
             uint32_t slot;
             gf2x_status st = plan_for(ctx, n, nullptr, &slot);
@@ -320,6 +320,7 @@ extern "C" gf2x_status gf2x_ctx_set_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_p
         }
         return GF2X_OK;
     }
+    // the current plan stays in force unless the new one is valid and installed
     gf2x_plan_info info;
     gf2x_status st = build_plan(n, spec, nullptr, &info);
     if (st != GF2X_OK)
@@ -328,6 +329,8 @@ extern "C" gf2x_status gf2x_ctx_set_plan(gf2x_ctx *ctx, uint32_t n, const gf2x_p
     st = install_plan(ctx, n, *spec, ctx->checked, nullptr, &s);
     if (st != GF2X_OK)
         return st;
+    ctx->by_n.erase(n);
+    ctx->by_n_checked.erase(n);
     (ctx->checked ? ctx->by_n_checked : ctx->by_n)[n] = PlanEntry{s, *spec};
     if (in_device_set(ctx, n)) {
         st = publish_plan(ctx, n, s, nullptr);

@@ -188,6 +188,7 @@ class Context:
         if st:
             raise Gf2xError(st, "gf2x_ctx_create")
         self._h = h
+        self.plan_db = plan_db
         if plan_db == "packaged":
             plan_db = PACKAGED_PLAN_DB if os.path.exists(PACKAGED_PLAN_DB) else None
         if plan_db:
