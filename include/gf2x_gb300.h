@@ -235,9 +235,12 @@ gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, size_t count
  *    copy, whichever call (and stream) made them.  `stream` waits for the
  *    last result copy: synchronize it before reading `out`; the caller must
  *    not change a or b, nor read out, until then.
- *  - Memory: the device buffers grow to 2 x (chunk products) x (2 stride_in
- *    + stride_out) limbs on the first call that needs more (cudaMalloc, which
- *    synchronizes the device) and are kept until gf2x_ctx_destroy.
+ *  - Rows: only the ceil(n/64) operand limbs of each row are read and only
+ *    the result limbs written; limbs between rows (strides above the sizes)
+ *    are left untouched.
+ *  - Memory: the device buffers grow to 2 x (chunk products) x (2 ceil(n/64)
+ *    + result limbs) limbs on the first call that needs more (cudaMalloc,
+ *    which synchronizes the device) and are kept until gf2x_ctx_destroy.
  *  - Errors: as gf2x_mul_strided (GF2X_EINVAL for null or overlapping host
  *    ranges, bad strides or flags); after a GF2X_ECUDA the results are
  *    undefined. */

@@ -640,6 +640,15 @@ extern "C" gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint
                   (batch_flags & GF2X_BATCH_PERSISTENT) != 0, s);
 }
 
+// k rows of `width` limbs, `dpitch` / `spitch` limbs apart.
+static cudaError_t copy_rows(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, size_t k,
+                             cudaMemcpyKind kind, cudaStream_t st)
+{
+    if (dpitch == width && spitch == width)
+        return cudaMemcpyAsync(dst, src, 8 * width * k, kind, st);
+    return cudaMemcpy2DAsync(dst, 8 * dpitch, src, 8 * spitch, 8 * width, k, kind, st);
+}
+
 static gf2x_status host_pipe_ready(gf2x_ctx *ctx, size_t bytes)
 {
     HostPipe &hp = ctx->hp;
@@ -692,10 +701,11 @@ extern "C" gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const
         return st;
     const size_t L = (n + 63) / 64;
     const size_t Lo = (flags & GF2X_REDUCE) ? L : (size_t)((2ull * n - 1 + 63) / 64);
-    const size_t si = count > 1 ? stride_in : L, so = count > 1 ? stride_out : Lo;   // device strides
+    // host strides (a single row may have any stride); the device rows are packed
+    const size_t hi = count > 1 ? stride_in : L, ho = count > 1 ? stride_out : Lo;
     const size_t nchunk = count >= 2048 ? 4 : (count >= 512 ? 2 : 1);
     const size_t K = (count + nchunk - 1) / nchunk;
-    const size_t in_w = K * si, set_w = 2 * in_w + K * so;
+    const size_t in_w = K * L, set_w = 2 * in_w + K * Lo;
     st = host_pipe_ready(ctx, 2 * set_w * sizeof(uint64_t));
     if (st != GF2X_OK)
         return st;
@@ -713,13 +723,14 @@ extern "C" gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const
         const int p = (int)(c & 1);
         const size_t k = std::min(K, count - c0);
         uint64_t *da = hp.buf + p * set_w, *db = da + in_w, *dout = db + in_w;
-        const size_t in_bytes = 8 * ((k - 1) * si + L), out_bytes = 8 * ((k - 1) * so + Lo);
         // the set's previous product (this call or an earlier one) has read its operands
         e = cudaStreamWaitEvent(hp.h2d, hp.done[p], 0);
+        // packed host rows: one flat copy; padded rows: one pitched copy moving
+        // only the L limbs of each row
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(da, a + c0 * si, in_bytes, cudaMemcpyHostToDevice, hp.h2d);
+            e = copy_rows(da, L, a + c0 * hi, hi, L, k, cudaMemcpyHostToDevice, hp.h2d);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(db, b + c0 * si, in_bytes, cudaMemcpyHostToDevice, hp.h2d);
+            e = copy_rows(db, L, b + c0 * hi, hi, L, k, cudaMemcpyHostToDevice, hp.h2d);
         if (e == cudaSuccess)
             e = cudaEventRecord(hp.in[p], hp.h2d);
         if (e == cudaSuccess)
@@ -728,14 +739,14 @@ extern "C" gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const
             e = cudaStreamWaitEvent(s, hp.out[p], 0);
         if (e != cudaSuccess)
             return cuda_fail(ctx, e, "host pipeline copy in");
-        st = gf2x_mul_strided(ctx, dout, da, db, n, k, si, so, flags, GF2X_BATCH_PERSISTENT, stream);
+        st = gf2x_mul_strided(ctx, dout, da, db, n, k, L, Lo, flags, GF2X_BATCH_PERSISTENT, stream);
         if (st != GF2X_OK)
             return st;
         e = cudaEventRecord(hp.done[p], s);
         if (e == cudaSuccess)
             e = cudaStreamWaitEvent(hp.d2h, hp.done[p], 0);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(out + c0 * so, dout, out_bytes, cudaMemcpyDeviceToHost, hp.d2h);
+        if (e == cudaSuccess)   // the limbs between result rows are left as they are
+            e = copy_rows(out + c0 * ho, ho, dout, Lo, Lo, k, cudaMemcpyDeviceToHost, hp.d2h);
         if (e == cudaSuccess)
             e = cudaEventRecord(hp.out[p], hp.d2h);
         if (e != cudaSuccess)

@@ -82,3 +82,41 @@ def test_rejects_overlap_and_bad_strides():
         assert st == 1                                                     # GF2X_EINVAL: stride < limbs
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("n,count,stride_pad", [(1, 5, 0), (63, 3, 1), (64, 2049, 0), (131072, 3, 2), (100000, 1, 0)])
+def test_edge_sizes_and_padded_strides(n, count, stride_pad):
+    """Tiny and maximal n, one product, and host rows with padding limbs."""
+    from paper_2201_10473_gb300 import Context
+    ctx = Context(0, plan_db=None)
+    try:
+        L = wl.limbs(n)
+        a, b = wl.dense_pair(9500 + n, n, count)
+        pa = np.zeros((count, L + stride_pad), np.uint64)
+        pb = np.zeros_like(pa)
+        pa[:, :L], pb[:, :L] = a, b
+        pa[:, L:] = np.uint64(0xDEADBEEFDEADBEEF)          # padding limbs are never read as operand words
+        ha, hb = _host(pa, True), _host(pb, True)
+        out = torch.full((count, L + 1), -1, dtype=torch.int64).pin_memory()
+        stream = torch.cuda.Stream()
+        ctx.mul_strided_host(ha, hb, n, True, out=out, stream=stream)
+        stream.synchronize()
+        ref = ctx.mul_strided(to_dev(a), to_dev(b), n, True).cpu()
+        assert torch.equal(out[:, :L], ref)
+        assert bool((out[:, L] == -1).all())                 # the column past the result is untouched
+        for p in (0, count - 1):
+            assert np.array_equal(out[p, :L].numpy().view(np.uint64), oracle.mulmod(a[p], b[p], n))
+    finally:
+        ctx.close()
+
+
+def test_zero_count_is_a_no_op():
+    from paper_2201_10473_gb300 import Context
+    ctx = Context(0, plan_db=None)
+    try:
+        n = 17669
+        e = torch.zeros((0, wl.limbs(n)), dtype=torch.int64)
+        got = ctx.mul_strided_host(e, e.clone(), n, True)
+        assert got.shape == (0, wl.limbs(n))
+    finally:
+        ctx.close()
