@@ -514,6 +514,10 @@ def run_c3(device):
     pa, pb = reqs.ptrs(np.arange(len(sizes)))
     po = np.array([outs[int(n)].data_ptr() + int(i) * 8 * wl.limbs(int(n)) for n, i in zip(sizes, reqs.index)])
     items = pack_items(list(zip(pa, pb, po, sizes, [1] * len(sizes)))).cuda()
+    # the same items largest first: a persistent CTA takes items i, i + grid, ...,
+    # so a sorted list hands every CTA one item of each size band in turn
+    by_size = np.argsort(-sizes, kind="stable")
+    items_lf = items[torch.from_numpy(by_size).cuda()].contiguous()
     log = autotune.packaged_log()
     best = None
     for plans in autotune.mixed_plan_sets(log, weights, 2048, top=3):
@@ -529,11 +533,18 @@ def run_c3(device):
         with torch.cuda.graph(g, stream=stream):
             ctx.mul_batched_device(items, len(sizes), persistent=True)
         ms = _time_calls(g.replay, 10, 3)
+        with torch.cuda.stream(stream):
+            ctx.mul_batched_device(items_lf, len(sizes), persistent=True)
+        torch.cuda.synchronize()
+        g_lf = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_lf, stream=stream):
+            ctx.mul_batched_device(items_lf, len(sizes), persistent=True)
+        ms_lf = _time_calls(g_lf.replay, 10, 3)
         ctx.sync_status()
-        if best is None or ms < best[0]:
-            best = (ms, plans)
+        if best is None or ms_lf < best[2]:
+            best = (ms, plans, ms_lf)
         ctx.close()
-    ms, plans = best
+    ms, plans, ms_lf = best
     # recompute with the best set and check a sample against the oracle
     ctx = Context(device, plan_db=None)
     for n, sp in plans.items():
@@ -541,7 +552,7 @@ def run_c3(device):
     ctx.prepare(sorted(int(n) for n in weights))
     for o in outs.values():
         o.zero_()
-    ctx.mul_batched_device(items, len(sizes), persistent=True)
+    ctx.mul_batched_device(items_lf, len(sizes), persistent=True)
     torch.cuda.synchronize()
     ok = True
     for r in range(0, len(sizes), 149):
@@ -596,6 +607,7 @@ def run_c3(device):
     total = len(sizes)
     return {"workload": wk.name, "products": total, "plans": {str(k): v for k, v in plans.items()},
             "one_launch_graph_mults_per_s": total / (ms * 1e-3),
+            "one_launch_graph_largest_first_mults_per_s": total / (ms_lf * 1e-3),
             "plain_mults_per_s": total / (ms_plain * 1e-3),
             "per_size_launches_mults_per_s": total / (ms_grouped * 1e-3),
             "one_graph_concurrent_per_size_kernels_mults_per_s": total / (ms_graph * 1e-3),

@@ -246,6 +246,10 @@ class Server:
                     sel = szs == n
                     addrs[sel] = self.pool.take_many(int(n), int(sel.sum()))
                 head += k
+                # largest first in the item array: the persistent CTAs take items
+                # i, i + grid, ..., so every CTA gets one item of each size band
+                lf = np.argsort(-szs, kind="stable")
+                rs, szs, addrs = rs[lf], szs[lf], addrs[lf]
                 s = free_streams.popleft()
                 pa, pb = reqs.ptrs(rs)
                 B = self._bucket(k) if self.use_graphs else k
