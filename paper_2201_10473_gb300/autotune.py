@@ -330,7 +330,14 @@ def main(argv=None):
                                                      "('packaged' = the shipped GB300 log)")
     p.add_argument("--top", type=int, default=60)
     p.add_argument("--split-from", type=int, default=24000, help="also try split-top plans from this size on")
+    p.add_argument("--guided", type=int, default=0,
+                   help="measure only the K candidates a cost model (trained on the packaged log) ranks first")
     a = p.parse_args(argv)
+    model = None
+    if a.guided:
+        from . import costmodel
+        model = costmodel.CostModel(seed=a.seed)
+        model.fit(packaged_log())
     prior = None
     if a.from_log:
         prior = packaged_log() if a.from_log == "packaged" else read_log(a.from_log)
@@ -345,6 +352,8 @@ def main(argv=None):
         if prior is not None:
             ranked = sorted((r for r in prior if r["n"] == n and r["batch"] == batches[0]), key=lambda r: r["ms"])
             cands = list(dict.fromkeys(r["spec"] for r in ranked))[: a.top] or cands
+        if model is not None:
+            cands = model.rank(n, batches[0], cands)[: a.guided]
         t0 = time.time()
         res = tuner.search(n, batches[0], cands, a.budget)
         if not res:

@@ -98,3 +98,24 @@ def test_learned_model_beats_unguided_search(holdout):
     r = costmodel.evaluate_gain(autotune.packaged_log(), holdout, 2048, k=10, steps=3000)
     assert r["model_measurements_to_5pct"] * 4 <= r["random_expected_measurements_to_5pct"], r
     assert r["regret_top_k"] <= 0.10, r
+
+
+def test_guided_search_on_an_unseen_size():
+    """Live on the GPU, at a size the timing log never saw: the network
+    (trained on the log) picks 10 candidates to measure, and the best of them
+    is within 10% of the best of an exhaustive measured search over all of
+    them (several thousand) -- the regret check of the learned part."""
+    from paper_2201_10473_gb300 import Context, autotune, costmodel
+    n, batch = 30011, 2048
+    model = costmodel.CostModel(seed=1)
+    model.fit(autotune.packaged_log(), steps=3000)
+    tuner = autotune.Autotuner(Context(0, plan_db=None), None, reps=3, warmup=1)
+    try:
+        cands = autotune.candidate_specs(n)
+        guided = tuner.search(n, batch, model.rank(n, batch, cands)[:10])
+        full = tuner.search(n, batch, cands)
+        assert guided and len(full) > 100 * len(guided) // 10
+        best = full[0].ms
+        assert guided[0].ms <= 1.10 * best, (guided[0].spec, guided[0].ms, full[0].spec, best)
+    finally:
+        tuner.ctx.close()
