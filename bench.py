@@ -362,25 +362,33 @@ def run_ours(args, w):
     got_e2e = pin_out.numpy().view(np.uint64)
     e2e_value = shard.whole_job_rate(batch * K2, world, e2e_ms * 1e-3)
 
-    # ---- plain form: one launch of one CTA per product
+    # ---- plain form: one launch of one CTA per product, with the plan tuned
+    # for a single product per launch
     plain = None
     if not args.no_plain:
+        from paper_2201_10473_gb300 import autotune
         a, b = sets[0]
         outs1 = out
+        cp = Context(local, plan_db=None)
+        single = autotune.single_product_plans([n]).get(n)
+        if single:
+            cp.set_plan(n, single)
         for _ in range(2):
             for p in range(batch):
-                (ctx.mulmod if reduce else ctx.mul)(a[p], b[p], n, out=outs1[p], stream=stream)
+                (cp.mulmod if reduce else cp.mul)(a[p], b[p], n, out=outs1[p], stream=stream)
         torch.cuda.synchronize()
         p0 = torch.cuda.Event(enable_timing=True)
         p1 = torch.cuda.Event(enable_timing=True)
         p0.record(stream)
         for p in range(batch):
-            (ctx.mulmod if reduce else ctx.mul)(a[p], b[p], n, out=outs1[p], stream=stream)
+            (cp.mulmod if reduce else cp.mul)(a[p], b[p], n, out=outs1[p], stream=stream)
         p1.record(stream)
         torch.cuda.synchronize()
         plain_ms = p0.elapsed_time(p1)
         plain = {"value": batch / (plain_ms * 1e-3), "unit": "mults/s", "launches": batch,
-                 "note": "one launch of one CTA per product, same plan"}
+                 "plan": cp.get_plan(n),
+                 "note": "one launch of one CTA per product, the plan tuned for one product per launch"}
+        cp.close()
 
     if rank != 0:
         if world > 1:
@@ -473,20 +481,30 @@ def run_c1(device):
 
     import oracle
     from paper_2201_10473_gb300 import Context
+    from paper_2201_10473_gb300 import autotune
     n, count = 12323, 256
     ctx = Context(device, batch_hint=count)
+    cp = Context(device, plan_db=None)            # the plan tuned for one product per launch
+    single = autotune.single_product_plans([n]).get(n)
+    if single:
+        cp.set_plan(n, single)
     a, b = wl.dense_pair(wl.BASE_SEED + 1, n, count)
     da, db = _dev(a), _dev(b)
     out = torch.empty((count, (2 * n - 1 + 63) // 64), dtype=torch.int64, device="cuda")
 
     def plain():
         for p in range(count):
-            ctx.mul(da[p], db[p], n, out=out[p])
+            cp.mul(da[p], db[p], n, out=out[p])
     ms = _time_calls(plain, 3, 1)
     ok = bool(np.array_equal(_host(out), oracle.mul_batch(a, b, n, reduce=False)))
+    out.zero_()
     ms_b = _time_calls(lambda: ctx.mul_strided(da, db, n, False, out=out, persistent=True), 10, 3)
+    ok &= bool(np.array_equal(_host(out), oracle.mul_batch(a, b, n, reduce=False)))
+    plain_plan = cp.get_plan(n)
     ctx.close()
+    cp.close()
     return {"workload": "plain-12323-full", "n": n, "products": count, "plan": ctx_plan_text(n, count),
+            "plain_plan": plain_plan,
             "plain_mults_per_s": count / (ms * 1e-3), "batched_mults_per_s": count / (ms_b * 1e-3),
             "all_checked_against_oracle": ok}
 
@@ -559,12 +577,17 @@ def run_c3(device):
         n, i = int(sizes[r]), int(reqs.index[r])
         got = _host(outs[n][i])
         ok &= bool(np.array_equal(got, oracle.mulmod(_host(reqs.a[n][i]), _host(reqs.b[n][i]), n)))
-    # plain: one launch of one CTA per product
+    # plain: one launch of one CTA per product, the single-product plans
+    cp = Context(device, plan_db=None)
+    for n, sp in autotune.single_product_plans([int(x) for x in weights]).items():
+        cp.set_plan(int(n), sp)
+
     def plain():
         for r in range(len(sizes)):
             n, i = int(sizes[r]), int(reqs.index[r])
-            ctx.mulmod(reqs.a[n][i], reqs.b[n][i], n, out=outs[n][i])
+            cp.mulmod(reqs.a[n][i], reqs.b[n][i], n, out=outs[n][i])
     ms_plain = _time_calls(plain, 1, 1)
+    cp.close()
     ctx.close()
     # per-size launches with each size's own tuned plan, one after the other
     ctx2 = Context(device, batch_hint=2048)
@@ -711,6 +734,8 @@ def run_c5(device, requests):
     m = min(4000, len(sizes))
     sub_reqs = serve.RequestSet(reqs.sizes[:m], reqs.index[:m], reqs.a, reqs.b)
     pool = serve.SlotPool(weights, budget)
+    # (the single-product plans, tuned for one launch at a time, serve three
+    # concurrent streams of launches more slowly than these plans: 22.5 k/s)
     pc = serve.serve_plain(ctx, sub_reqs, np.zeros(m), pool, streams=3)
     pcap = pc.completed / pc.wall_s
     arr = wl.poisson_arrivals(wk.seed + 7, m, 0.8 * pcap)

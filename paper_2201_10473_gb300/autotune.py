@@ -248,6 +248,18 @@ def mixed_plan_sets(records: list, weights: dict, batch: int, top: int = 3) -> l
 
 
 PACKAGED_TIMING_LOG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans", "gb300_timing_log.jsonl.gz")
+# exhaustive search of one product per launch (batch 1): the single-product plans
+PACKAGED_SINGLE_LOG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans",
+                                   "gb300_timing_log_batch1.jsonl.gz")
+
+
+def single_product_plans(sizes, one_launch: bool = True) -> dict:
+    """Fastest plan for one product per launch of every size, from the batch-1
+    timing log; one_launch excludes split plans (three launches)."""
+    import gzip
+    with gzip.open(PACKAGED_SINGLE_LOG, "rt") as f:
+        recs = [json.loads(line) for line in f if line.strip()]
+    return best_plans(recs, sizes, 1, allow_split=not one_launch)
 
 
 def packaged_log() -> list:
