@@ -24,3 +24,23 @@ def test_rejected_plan_keeps_the_current_one():
         assert torch.equal(r, ctx.mul_strided(to_dev(a), to_dev(b), n, True))
     finally:
         ctx.close()
+
+
+def test_single_product_plans_from_the_database():
+    """batch_hint=1 selects the database's single-product (batch 1) plans --
+    split plans, three launches over 15 CTAs -- and they give the oracle's
+    product."""
+    import numpy as np
+
+    import oracle
+    from paper_2201_10473_gb300 import Context, autotune, gf2x
+    db = autotune.load_db(gf2x.PACKAGED_PLAN_DB)
+    ctx = Context(0, batch_hint=1)
+    try:
+        for n in (12323, 57637):
+            assert ctx.get_plan(n) == db[(n, 1)]["spec"]
+            a, b = wl.dense_pair(73 + n, n, 1)
+            r = ctx.mulmod(to_dev(a)[0], to_dev(b)[0], n)
+            assert np.array_equal(r.cpu().numpy().view(np.uint64), oracle.mulmod(a[0], b[0], n))
+    finally:
+        ctx.close()
