@@ -212,7 +212,9 @@ gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, co
  *    checked on the host and nothing is copied, so the call can be captured
  *    in a CUDA graph; the array must stay valid until the work completes.
  *  - GF2X_BATCH_PERSISTENT: a grid of (SMs x resident CTAs), each CTA
- *    looping over items; otherwise one CTA per item.
+ *    looping over items i, i + grid, i + 2 grid, ...; otherwise one CTA per
+ *    item.  Items of uneven sizes balance best ordered largest first (every
+ *    CTA then draws one item of each size band per round).
  *  - GF2X_BATCH_LARGEST_FIRST (host items): larger n first. */
 gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, size_t count,
                              uint32_t batch_flags, gf2x_stream stream);
