@@ -96,6 +96,9 @@ class SlotPool:
             self.top[n] = share
             off += share * L
         self.capacity = dict(self.top)
+        empty = [n for n, c in self.capacity.items() if c == 0]
+        if empty:   # requests of such a size could never be admitted
+            raise ValueError(f"budget too small: no output slot for sizes {empty}")
 
     def available(self, n: int) -> int:
         return self.top.get(n, 0)

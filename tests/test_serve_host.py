@@ -43,3 +43,9 @@ def test_slot_pool_take_and_give_many_conserve_slots():
     assert pool.available(n) == cap - 9
     c = pool.take_many(n, cap - 9)
     assert set(c.tolist()) == set(b.tolist()) | {int(a[0])}
+
+
+def test_slot_pool_rejects_a_budget_without_a_slot_for_some_size():
+    import pytest
+    with pytest.raises(ValueError):
+        serve.SlotPool({12323: 1, 57637: 1}, 8000, device="cpu")   # 4000 bytes each: no 57637 slot
