@@ -206,6 +206,9 @@ class Server:
         each retired batch (before its slots are reused) if given."""
         torch = self.torch
         N = len(reqs)
+        unknown = set(np.unique(reqs.sizes).tolist()) - set(self.pool.capacity)
+        if unknown:
+            raise ValueError(f"no output slots for request sizes {sorted(unknown)}")
         order = np.argsort(arrivals, kind="stable")
         arr = arrivals[order]
         osz = reqs.sizes[order]
@@ -433,6 +436,9 @@ def serve_plain(ctx: gf2x.Context, reqs: RequestSet, arrivals: np.ndarray, pool:
     """Baseline: one launch (one CTA) per request on arrival, round-robin over streams."""
     import torch
     N = len(reqs)
+    unknown = set(np.unique(reqs.sizes).tolist()) - set(pool.capacity)
+    if unknown:
+        raise ValueError(f"no output slots for request sizes {sorted(unknown)}")
     order = np.argsort(arrivals, kind="stable")
     arr = arrivals[order]
     ss = [torch.cuda.Stream() for _ in range(streams)]
