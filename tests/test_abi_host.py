@@ -160,3 +160,26 @@ def test_split_plan_facts():
     whole = gf2x.plan_info(57637, "T16.K5.K2.K2.K2.K2/8/0/1/1/0")
     assert whole["nleaves"] == info["nleaves"]
     assert gf2x.plan_info(131072, None)["scratch_bytes"] > 0      # only split plans reach the maximum size
+
+
+def test_packaged_plan_database_and_logs_are_consistent():
+    """Every database entry is a valid plan for its size and is the fastest
+    record of its (size, bucket) in the shipped timing logs; the single-
+    product plans chosen for the plain baselines are one-launch plans."""
+    import gzip
+    import json
+
+    from paper_2201_10473_gb300 import autotune
+    db = autotune.load_db(gf2x.PACKAGED_PLAN_DB)
+    recs = autotune.packaged_log()
+    with gzip.open(autotune.PACKAGED_SINGLE_LOG, "rt") as f:
+        recs += [json.loads(line) for line in f if line.strip()]
+    assert len(db) >= 24
+    for (n, bucket), e in db.items():
+        info = gf2x.plan_info(n, e["spec"])
+        assert 32 * info["top_words"] >= n
+        same = [r for r in recs if r["n"] == n and autotune.batch_bucket(r["batch"]) == bucket]
+        assert same, (n, bucket)
+        assert min(same, key=lambda r: r["ms"])["spec"] == e["spec"], (n, bucket)
+    single = autotune.single_product_plans([12323, 17669, 24659, 35851, 40973, 57637])
+    assert len(single) == 6 and all(not s.endswith("/1") for s in single.values())
