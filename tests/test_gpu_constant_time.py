@@ -5,6 +5,8 @@ ones, sparse weight 131): launch times agree within a few percent, and the
 results stay bit-exact (sampled against the oracle).  The structural
 argument (no operand-dependent branch or address) is in the kernel source;
 this is the measured side of it."""
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -48,13 +50,25 @@ def test_launch_time_independent_of_operand_bits(n):
             "sparse131": (dense_a, wl.sparse_operands(6001, n, 131, count)),
         }
         out = torch.empty((count, L), dtype=torch.int64, device="cuda")
-        ms = {}
-        for name, (a, b) in classes.items():
-            da, db = to_dev(a), to_dev(b)
-            ms[name] = _median_launch_ms(ctx, da, db, n, out)
-            got = to_host(out)
-            sample = np.arange(0, count, 512)
-            assert np.array_equal(got[sample], oracle.mul_batch(a[sample], b[sample], n, reduce=True)), name
+        dev = {name: (to_dev(a), to_dev(b)) for name, (a, b) in classes.items()}
+        sample = np.arange(0, count, 512)
+        for name, (da, db) in dev.items():
+            ctx.mul_strided(da, db, n, True, out=out, persistent=True)
+            a, b = classes[name]
+            assert np.array_equal(to_host(out)[sample], oracle.mul_batch(a[sample], b[sample], n, reduce=True)), name
+        # a second of launches first, so that no class is timed while the
+        # clock still ramps up; then the classes in turn, three rounds, the
+        # fastest median of each (a clock dip only slows its own round)
+        da, db = dev["dense"]
+        t_end = time.time() + 1.0
+        while time.time() < t_end:
+            ctx.mul_strided(da, db, n, True, out=out, persistent=True)
+            torch.cuda.synchronize()
+        rounds = {name: [] for name in dev}
+        for _ in range(3):
+            for name, (da, db) in dev.items():
+                rounds[name].append(_median_launch_ms(ctx, da, db, n, out))
+        ms = {name: min(t) for name, t in rounds.items()}
         spread = max(ms.values()) / min(ms.values())
         assert spread < 1.05, ms
     finally:
