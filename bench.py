@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="hqc128")
     p.add_argument("--no-plain", action="store_true", help="skip the plain one-launch-per-product measurement")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle cpu_baseline sample")
-    p.add_argument("--no-extras", action="store_true", help="skip the other workloads (C1, C3, C4, C5)")
+    p.add_argument("--no-extras", action="store_true", help="skip the other workloads (C1, C3, C4, shared key, C5)")
     p.add_argument("--serving-requests", type=int, default=200000)
     p.add_argument("--plan", default=None, help="plan spec for the main workload (default: the tuned database)")
     return p.parse_args()
@@ -665,6 +665,47 @@ def run_c4(device):
             "sample_checked_against_oracle": ok}
 
 
+def run_shared(device):
+    """One public key h times many vectors at n = 17669 (reduced mod X^n - 1),
+    shared-operand launch against the unshared launch with h copied into every
+    row; 4096 products per launch, 8 rotating input sets (> L2)."""
+    import torch
+
+    import oracle
+    from paper_2201_10473_gb300 import Context
+    n, count, R = 17669, 4096, 8
+    ctx = Context(device, batch_hint=count)
+    h = wl.dense_operands(wl.BASE_SEED + 8, n, 1, 0)
+    vecs = [wl.dense_operands(wl.BASE_SEED + 8, n, count, 1, first=r * count) for r in range(R)]
+    dh, dhs = _dev(h[0]), _dev(np.repeat(h, count, axis=0))
+    dv = [_dev(v) for v in vecs]
+    out = torch.empty((count, wl.limbs(n)), dtype=torch.int64, device="cuda")
+    it = [0]
+
+    def call(a_of):
+        r = it[0] % R
+        it[0] += 1
+        ctx.mul_strided(a_of(r), dv[r], n, True, out=out, persistent=True)
+    rates = {}
+    for rep in range(3):        # interleaved: shared, unshared, shared, ...
+        for name, a_of in (("shared", lambda r: dh), ("unshared", lambda r: dhs)):
+            it[0] = 0
+            ms = _time_calls(lambda: call(a_of), 40, 3)
+            rates.setdefault(name, []).append(count / (ms * 1e-3))
+    it[0] = 0
+    call(lambda r: dh)
+    sample = np.arange(0, count, 512)
+    ok = bool(np.array_equal(_host(out)[sample], np.stack([oracle.mulmod(h[0], vecs[0][p], n) for p in sample])))
+    plan = ctx.get_plan(n)
+    ctx.close()
+    shared, unshared = max(rates["shared"]), max(rates["unshared"])
+    return {"workload": "shared-key-17669-mulmod", "products": count, "plan": plan,
+            "shared_mults_per_s": shared, "unshared_mults_per_s": unshared, "shared_over_unshared": shared / unshared,
+            "note": "one a for every product (GF2X_BATCH_SHARED_A); the product is ALU-bound, so sharing saves "
+                    "memory reads, not time",
+            "sample_checked_against_oracle": ok}
+
+
 def run_c5(device, requests):
     """Serving: Poisson arrivals, HBM-budget admission, continuous batching."""
     import torch  # noqa: F401
@@ -748,6 +789,7 @@ def run_c5(device, requests):
 def run_extras(args, device):
     res = {}
     for name, fn in (("c1", lambda: run_c1(device)), ("c3", lambda: run_c3(device)), ("c4", lambda: run_c4(device)),
+                     ("shared_key", lambda: run_shared(device)),
                      ("c5", lambda: run_c5(device, args.serving_requests))):
         t0 = time.time()
         try:

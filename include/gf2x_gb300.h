@@ -63,6 +63,7 @@ typedef enum {
 #define GF2X_BATCH_PERSISTENT 1u  /* grid of (SMs x resident CTAs); each CTA loops over the items */
 #define GF2X_BATCH_ITEMS_ON_DEVICE 2u /* `items` points to device memory (gf2x_item array) */
 #define GF2X_BATCH_LARGEST_FIRST 4u   /* order items by decreasing n (sizes are public) before the launch */
+#define GF2X_BATCH_SHARED_A 8u        /* gf2x_mul_strided: one a for every product (a fixed key polynomial) */
 
 /*
  * A recursion plan: `nlev` split levels from the top down, then a leaf of
@@ -187,8 +188,13 @@ gf2x_status gf2x_mulmod_xn1(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a, const
 
 /* `count` independent products of one size n in one launch.  Operand p is
  * a + p*stride_in, result p is out + p*stride_out (strides in limbs, at
- * least ceil(n/64) and the output size).  flags: GF2X_REDUCE, and
- * GF2X_BATCH_PERSISTENT in batch_flags. */
+ * least ceil(n/64) and the output size).  flags: GF2X_REDUCE; batch_flags:
+ * GF2X_BATCH_PERSISTENT, and GF2X_BATCH_SHARED_A, with which every product
+ * reads the same a (its ceil(n/64) limbs; only b advances by stride_in),
+ * as when one public-key polynomial of the HQC/BIKE operations of Sec. 1
+ * serves many encapsulations.  The results are those of the unshared call
+ * with a copied into every row; the saving is a's reads from memory (a
+ * stays in L2), not arithmetic. */
 gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b,
                              uint32_t n, size_t count, size_t stride_in, size_t stride_out,
                              uint32_t flags, uint32_t batch_flags, gf2x_stream stream);

@@ -386,7 +386,8 @@ static bool ranges_overlap(const void *p, size_t pbytes, const void *q, size_t q
 }
 
 static gf2x_status check_operands(gf2x_ctx *ctx, const uint64_t *out, const uint64_t *a, const uint64_t *b,
-                                  uint32_t n, uint32_t flags, size_t count, size_t stride_in, size_t stride_out)
+                                  uint32_t n, uint32_t flags, size_t count, size_t stride_in, size_t stride_out,
+                                  bool shared_a = false)
 {
     if (!out || !a || !b)
         return fail(ctx, GF2X_EINVAL, "null operand or result pointer");
@@ -400,7 +401,7 @@ static gf2x_status check_operands(gf2x_ctx *ctx, const uint64_t *out, const uint
         return fail(ctx, GF2X_EINVAL, "stride smaller than the operand or result size");
     const size_t in_bytes = 8 * ((count - 1) * stride_in + L);
     const size_t out_bytes = 8 * ((count - 1) * stride_out + Lo);
-    if (ranges_overlap(out, out_bytes, a, in_bytes) || ranges_overlap(out, out_bytes, b, in_bytes))
+    if (ranges_overlap(out, out_bytes, a, shared_a ? 8 * L : in_bytes) || ranges_overlap(out, out_bytes, b, in_bytes))
         return fail(ctx, GF2X_EINVAL, "result overlaps an operand");
     return GF2X_OK;
 }
@@ -486,7 +487,8 @@ static gf2x_status run_split_on(gf2x_ctx *ctx, uint32_t top_slot, uint32_t *ws, 
         const size_t k = std::min(chunk, count - c0);
         LaunchArgs ta = top;
         if (ta.mode == kItemsStrided) {
-            ta.base.a += c0 * ta.stride_in;
+            if (!ta.shared_a)
+                ta.base.a += c0 * ta.stride_in;
             ta.base.b += c0 * ta.stride_in;
             ta.base.out += c0 * ta.stride_out;
         } else {
@@ -549,7 +551,7 @@ static gf2x_status run_split_args(gf2x_ctx *ctx, uint32_t top_slot, const Launch
 
 static gf2x_status run_split(gf2x_ctx *ctx, uint32_t top_slot, uint64_t *out, const uint64_t *a, const uint64_t *b,
                              size_t count, size_t stride_in, size_t stride_out, uint32_t flags, bool persistent,
-                             cudaStream_t stream)
+                             cudaStream_t stream, bool shared_a = false)
 {
     LaunchArgs ta;
     memset(&ta, 0, sizeof(ta));
@@ -558,6 +560,7 @@ static gf2x_status run_split(gf2x_ctx *ctx, uint32_t top_slot, uint64_t *out, co
     ta.stride_in = stride_in;
     ta.stride_out = stride_out;
     ta.mode = kItemsStrided;
+    ta.shared_a = shared_a ? 1u : 0u;
     return run_split_args(ctx, top_slot, ta, count, persistent, stream);
 }
 
@@ -611,9 +614,10 @@ extern "C" gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint
         return GF2X_OK;
     if (n < 1 || n > GF2X_MAX_N)
         return fail(ctx, GF2X_EUNSUPPORTED, "n outside [1, 131072]");
-    if (batch_flags & ~(uint32_t)GF2X_BATCH_PERSISTENT)
+    if (batch_flags & ~(uint32_t)(GF2X_BATCH_PERSISTENT | GF2X_BATCH_SHARED_A))
         return fail(ctx, GF2X_EINVAL, "unknown batch flag");
-    gf2x_status st = check_operands(ctx, out, a, b, n, flags, count, stride_in, stride_out);
+    const bool shared_a = (batch_flags & GF2X_BATCH_SHARED_A) != 0;
+    gf2x_status st = check_operands(ctx, out, a, b, n, flags, count, stride_in, stride_out, shared_a);
     if (st != GF2X_OK)
         return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -624,7 +628,7 @@ extern "C" gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint
     const GPlan &P = ctx->plans_host[slot];
     if (P.split)
         return run_split(ctx, slot, out, a, b, count, stride_in, stride_out, flags,
-                         (batch_flags & GF2X_BATCH_PERSISTENT) != 0, s);
+                         (batch_flags & GF2X_BATCH_PERSISTENT) != 0, s, shared_a);
     LaunchArgs args;
     memset(&args, 0, sizeof(args));
     args.plans = ctx->plans_dev;
@@ -633,6 +637,7 @@ extern "C" gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint
     args.stride_out = stride_out;
     args.count = (uint32_t)count;
     args.mode = kItemsStrided;
+    args.shared_a = shared_a ? 1u : 0u;
     args.err = ctx->err_dev;
     if (count > 0xffffffffull)
         return fail(ctx, GF2X_EINVAL, "batch too large");

@@ -697,7 +697,8 @@ __device__ __forceinline__ DevItem fetch_item(const LaunchArgs &args, uint32_t i
     }
     DevItem it = args.base;
     if (args.mode == kItemsStrided) {
-        it.a += (uint64_t)i * args.stride_in;
+        if (!args.shared_a)
+            it.a += (uint64_t)i * args.stride_in;
         it.b += (uint64_t)i * args.stride_in;
         it.out += (uint64_t)i * args.stride_out;
     }

@@ -91,7 +91,7 @@ struct LaunchArgs {
     uint32_t count;
     uint32_t mode;
     uint32_t persistent;
-    uint32_t pad_;
+    uint32_t shared_a;        // mode kItemsStrided: 1 = every product reads the same a
     uint32_t *err;            // device error word (checked mode), may be null
     const uint32_t *plan_of_n; // mode kItemsUser: plan slot of every n (kNoPlan if none)
 };

@@ -27,6 +27,7 @@ HOST_INPUTS_READY = 1 << 8
 BATCH_PERSISTENT = 1
 BATCH_ITEMS_ON_DEVICE = 2
 BATCH_LARGEST_FIRST = 4
+BATCH_SHARED_A = 8
 
 STATUS = {0: "GF2X_OK", 1: "GF2X_EINVAL", 2: "GF2X_ENOMEM", 3: "GF2X_ECUDA", 4: "GF2X_ETIMEOUT",
           5: "GF2X_EUNSUPPORTED", 6: "GF2X_EBUSY", 7: "GF2X_EDEVICE"}
@@ -262,20 +263,24 @@ class Context:
 
     def mul_strided(self, a: torch.Tensor, b: torch.Tensor, n: int, reduce: bool, out: torch.Tensor | None = None,
                     persistent: bool = False, stream=None):
-        """Row p of the result is the product of rows p of a and b (2-D tensors)."""
-        if a.dim() != 2 or a.shape != b.shape:
-            raise ValueError("a and b must be equal-shaped 2-D tensors")
+        """Row p of the result is the product of rows p of a and b (2-D
+        tensors).  A 1-D a is one operand shared by every row of b
+        (GF2X_BATCH_SHARED_A)."""
+        shared = a.dim() == 1
+        if b.dim() != 2 or (not shared and a.shape != b.shape):
+            raise ValueError("a and b must be equal-shaped 2-D tensors, or a 1-D a shared by the rows of b")
         _check_operand(a, n, "a")
         _check_operand(b, n, "b")
-        count = a.shape[0]
+        count = b.shape[0]
         ol = limbs(n) if reduce else full_limbs(n)
         if out is None:
-            out = torch.empty((count, ol), dtype=torch.int64, device=a.device)
+            out = torch.empty((count, ol), dtype=torch.int64, device=b.device)
         if out.dim() != 2 or out.shape[0] != count or out.shape[1] < ol or not out.is_contiguous():
             raise ValueError("bad output tensor")
+        bflags = (BATCH_PERSISTENT if persistent else 0) | (BATCH_SHARED_A if shared else 0)
         self._raise(lib().gf2x_mul_strided(self._h, out.data_ptr(), a.data_ptr(), b.data_ptr(), n, count,
-                                           a.shape[1], out.shape[1], REDUCE if reduce else 0,
-                                           BATCH_PERSISTENT if persistent else 0, _stream_handle(stream)),
+                                           b.shape[1], out.shape[1], REDUCE if reduce else 0,
+                                           bflags, _stream_handle(stream)),
                     "gf2x_mul_strided")
         return out
 
