@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="hqc128")
     p.add_argument("--no-plain", action="store_true", help="skip the plain one-launch-per-product measurement")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle cpu_baseline sample")
-    p.add_argument("--no-extras", action="store_true", help="skip the other workloads (C1, C3, C4, shared key, C5)")
+    p.add_argument("--no-extras", action="store_true", help="skip the other workloads (C1, C3, C4, shared key, unbalanced, C5)")
     p.add_argument("--serving-requests", type=int, default=200000)
     p.add_argument("--plan", default=None, help="plan spec for the main workload (default: the tuned database)")
     return p.parse_args()
@@ -706,6 +706,60 @@ def run_shared(device):
             "sample_checked_against_oracle": ok}
 
 
+def run_unbalanced(device):
+    """2048 full products of a 57637-bit a and a 17669-bit b through the
+    unbalanced entry (four 17728-bit chunk products and an overlap-add, as
+    the op model picks), against the equal-size 57637 product of the
+    zero-extended b; 4 rotating input sets (> L2)."""
+    import torch
+
+    import oracle
+    from paper_2201_10473_gb300 import Context
+    na, nb, count, R = 57637, 17669, 2048, 4
+    ctx = Context(device, batch_hint=count)
+    la, lb, lu = wl.limbs(na), wl.limbs(nb), (na + nb - 1 + 63) // 64
+    sets = []
+    for r in range(R):
+        a = wl.dense_operands(wl.BASE_SEED + 9, na, count, 0, first=r * count)
+        b = wl.dense_operands(wl.BASE_SEED + 9, nb, count, 1, first=r * count)
+        bz = np.zeros((count, la), np.uint64)
+        bz[:, :lb] = b
+        sets.append((a, b, _dev(a), _dev(b), _dev(bz)))
+    out = torch.empty((count, lu), dtype=torch.int64, device="cuda")
+    full = torch.empty((count, (2 * na - 1 + 63) // 64), dtype=torch.int64, device="cuda")
+    it = [0]
+
+    def unbalanced():
+        _, _, da, db, _ = sets[it[0] % R]
+        it[0] += 1
+        ctx.mul_unbalanced(da, na, db, nb, out=out)
+
+    def padded():
+        _, _, da, _, dbz = sets[it[0] % R]
+        it[0] += 1
+        ctx.mul_strided(da, dbz, na, False, out=full, persistent=True)
+    rates = {}
+    for rep in range(2):
+        for name, fn in (("unbalanced", unbalanced), ("padded", padded)):
+            it[0] = 0
+            ms = _time_calls(fn, 8, 3)
+            rates.setdefault(name, []).append(count / (ms * 1e-3))
+    it[0] = 0
+    unbalanced()
+    a, b = sets[0][0], sets[0][1]
+    got = _host(out)
+    ok = True
+    for p in range(0, count, 512):
+        bz = np.zeros(la, np.uint64)
+        bz[:lb] = b[p]
+        ok &= bool(np.array_equal(got[p], oracle.mul(a[p], bz, na)[:lu]))
+    ctx.close()
+    u, pz = max(rates["unbalanced"]), max(rates["padded"])
+    return {"workload": "unbalanced-57637x17669-full", "products": count,
+            "unbalanced_mults_per_s": u, "padded_equal_size_mults_per_s": pz, "speedup": u / pz,
+            "sample_checked_against_oracle": ok}
+
+
 def run_c5(device, requests):
     """Serving: Poisson arrivals, HBM-budget admission, continuous batching."""
     import torch  # noqa: F401
@@ -789,7 +843,7 @@ def run_c5(device, requests):
 def run_extras(args, device):
     res = {}
     for name, fn in (("c1", lambda: run_c1(device)), ("c3", lambda: run_c3(device)), ("c4", lambda: run_c4(device)),
-                     ("shared_key", lambda: run_shared(device)),
+                     ("shared_key", lambda: run_shared(device)), ("unbalanced", lambda: run_unbalanced(device)),
                      ("c5", lambda: run_c5(device, args.serving_requests))):
         t0 = time.time()
         try:

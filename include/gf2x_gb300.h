@@ -258,6 +258,29 @@ gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const uint64_t *
                                   uint32_t n, size_t count, size_t stride_in, size_t stride_out,
                                   uint32_t flags, gf2x_stream stream);
 
+/* `count` full products of operands of different sizes: row p of a (na
+ * bits in ceil(na/64) limbs, stride_a limbs apart) times row p of b (nb
+ * bits, stride_b), result row p of ceil((na + nb - 1)/64) limbs at out +
+ * p*stride_out.  Bits above na / nb in the operands' top limbs are ignored.
+ * With nb <= na (else the operands swap roles; the product commutes) the
+ * call runs either one equal-size product of the zero-extended operands
+ * (the padding of Sec. 3.2) or, when the context's plans model it cheaper,
+ * k = ceil(na/m) products of a's m-bit chunks times b, m = 64 ceil(nb/64),
+ * added at offsets i m (the one-sided split of Sec. 2.1):
+ * a padding kernel, the batched products, an overlap-add kernel, all on
+ * `stream`.  Without a plan of its own for m, the chunk products run under
+ * the spec of nb's plan where it covers m (same limb count; the context's
+ * plan for m is left unset).  Scratch: a device buffer of the context, grown on demand
+ * (cudaMalloc, which synchronizes the device) up to 256 MiB per group of
+ * products (larger batches run in groups) and kept until
+ * gf2x_ctx_destroy; calls on different streams are ordered through it.
+ * Errors: GF2X_EUNSUPPORTED for a size outside [1, 131072]; GF2X_EINVAL for
+ * null or misaligned pointers, short strides, results overlapping an
+ * operand. */
+gf2x_status gf2x_mul_unbalanced(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, uint32_t na, size_t stride_a,
+                                const uint64_t *b, uint32_t nb, size_t stride_b, size_t count, size_t stride_out,
+                                gf2x_stream stream);
+
 /* Build and upload (synchronously on `stream`) the current plans of the
  * given sizes, so that later calls and CUDA graph captures find them ready,
  * and make exactly these sizes the ones device-item batches accept (their

@@ -81,6 +81,11 @@ struct gf2x_ctx {
     cudaStream_t ws_stream = nullptr;
     bool ws_used = false;
     HostPipe hp;                                        // gf2x_mul_strided_host
+    uint64_t *ub = nullptr;                             // gf2x_mul_unbalanced: padded operands and products
+    size_t ub_bytes = 0;
+    cudaEvent_t ub_done = nullptr;                      // recorded after the last use of ub
+    cudaStream_t ub_stream = nullptr;
+    bool ub_used = false;
 };
 
 static std::string plan_key(uint32_t n, const gf2x_plan_spec &spec, int checked)
@@ -208,6 +213,10 @@ extern "C" void gf2x_ctx_destroy(gf2x_ctx *ctx)
         cudaFree(ctx->ws);
     if (ctx->ws_done)
         cudaEventDestroy(ctx->ws_done);
+    if (ctx->ub)
+        cudaFree(ctx->ub);
+    if (ctx->ub_done)
+        cudaEventDestroy(ctx->ub_done);
     HostPipe &hp = ctx->hp;
     if (hp.buf)
         cudaFree(hp.buf);
@@ -604,6 +613,10 @@ extern "C" gf2x_status gf2x_mulmod_xn1(gf2x_ctx *ctx, uint64_t *r, const uint64_
     return one_product(ctx, r, a, b, n, GF2X_REDUCE, stream);
 }
 
+static gf2x_status strided_on_slot(gf2x_ctx *ctx, uint32_t slot, uint64_t *out, const uint64_t *a,
+                                   const uint64_t *b, size_t count, size_t stride_in, size_t stride_out,
+                                   uint32_t flags, uint32_t batch_flags, cudaStream_t s);
+
 extern "C" gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b,
                                         uint32_t n, size_t count, size_t stride_in, size_t stride_out,
                                         uint32_t flags, uint32_t batch_flags, gf2x_stream stream)
@@ -625,6 +638,15 @@ extern "C" gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint
     st = plan_for(ctx, n, s, &slot);
     if (st != GF2X_OK)
         return st;
+    return strided_on_slot(ctx, slot, out, a, b, count, stride_in, stride_out, flags, batch_flags, s);
+}
+
+// The strided batch under plan `slot` (operands already checked).
+static gf2x_status strided_on_slot(gf2x_ctx *ctx, uint32_t slot, uint64_t *out, const uint64_t *a,
+                                   const uint64_t *b, size_t count, size_t stride_in, size_t stride_out,
+                                   uint32_t flags, uint32_t batch_flags, cudaStream_t s)
+{
+    const bool shared_a = (batch_flags & GF2X_BATCH_SHARED_A) != 0;
     const GPlan &P = ctx->plans_host[slot];
     if (P.split)
         return run_split(ctx, slot, out, a, b, count, stride_in, stride_out, flags,
@@ -643,6 +665,153 @@ extern "C" gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint
         return fail(ctx, GF2X_EINVAL, "batch too large");
     return launch(ctx, args, P.S, P.threads, 4ull * P.smem_words, count,
                   (batch_flags & GF2X_BATCH_PERSISTENT) != 0, s);
+}
+
+// The plan slot and modelled operations of a product of size n in an
+// unbalanced call: the context's current plan for n; for the chunk size m
+// (= 64 ceil(nb/64)) without a plan of its own, the spec of nb's plan where
+// it also covers m (the same limb count, so a plan tuned for nb serves its
+// chunk products), else the default.  A borrowed spec gets a slot of its
+// own but does not become the context's plan for m.
+static gf2x_status unbalanced_plan(gf2x_ctx *ctx, uint32_t n, uint32_t borrow_from, cudaStream_t s,
+                                   uint32_t *slot, uint64_t *ops)
+{
+    auto &map = ctx->checked ? ctx->by_n_checked : ctx->by_n;
+    gf2x_plan_info info;
+    gf2x_status st;
+    if (borrow_from && borrow_from != n && map.find(n) == map.end()) {
+        uint32_t unused;
+        st = plan_for(ctx, borrow_from, s, &unused);
+        if (st != GF2X_OK)
+            return st;
+        const gf2x_plan_spec spec = map.at(borrow_from).spec;
+        if (gf2x_plan_info_get(n, &spec, &info) == GF2X_OK &&
+            install_plan(ctx, n, spec, ctx->checked, s, slot) == GF2X_OK) {
+            *ops = info.ops_full;
+            return GF2X_OK;
+        }
+    }
+    st = plan_for(ctx, n, s, slot);
+    if (st != GF2X_OK)
+        return st;
+    st = gf2x_plan_info_get(n, &map.at(n).spec, &info);
+    if (st != GF2X_OK)
+        return fail(ctx, st, "plan description");
+    *ops = info.ops_full;
+    return GF2X_OK;
+}
+
+extern "C" gf2x_status gf2x_mul_unbalanced(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, uint32_t na,
+                                           size_t stride_a, const uint64_t *b, uint32_t nb, size_t stride_b,
+                                           size_t count, size_t stride_out, gf2x_stream stream)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    if (count == 0)
+        return GF2X_OK;
+    if (na < 1 || nb < 1 || na > GF2X_MAX_N || nb > GF2X_MAX_N)
+        return fail(ctx, GF2X_EUNSUPPORTED, "operand size outside [1, 131072]");
+    if (!out || !a || !b)
+        return fail(ctx, GF2X_EINVAL, "null operand or result pointer");
+    if (((uintptr_t)out | (uintptr_t)a | (uintptr_t)b) & 7u)
+        return fail(ctx, GF2X_EINVAL, "operands and results must be 8-byte aligned");
+    const size_t La = (na + 63) / 64, Lb = (nb + 63) / 64;
+    const uint32_t Lu = (uint32_t)(((uint64_t)na + nb - 1 + 63) / 64);
+    if (count > 1 && (stride_a < La || stride_b < Lb || stride_out < Lu))
+        return fail(ctx, GF2X_EINVAL, "stride smaller than the operand or result size");
+    const size_t out_bytes = 8 * ((count - 1) * stride_out + Lu);
+    if (ranges_overlap(out, out_bytes, a, 8 * ((count - 1) * stride_a + La)) ||
+        ranges_overlap(out, out_bytes, b, 8 * ((count - 1) * stride_b + Lb)))
+        return fail(ctx, GF2X_EINVAL, "result overlaps an operand");
+    if (na < nb) {   // the product commutes: a is the longer operand from here on
+        std::swap(a, b);
+        std::swap(na, nb);
+        std::swap(stride_a, stride_b);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // padded: one product of size na; chunked: k products of size m
+    const uint32_t Lc = (uint32_t)((nb + 63) / 64), m = 64u * Lc;
+    const uint32_t k = (na + m - 1) / m;
+    uint32_t size = na, chunks = 1, Ld = (uint32_t)((na + 63) / 64), step = 0, slot = 0;
+    uint64_t ops_pad = 0;
+    gf2x_status pst = unbalanced_plan(ctx, na, 0u, s, &slot, &ops_pad);
+    if (pst != GF2X_OK)
+        return pst;
+    if (k >= 2) {
+        uint32_t chunk_slot = 0;
+        uint64_t ops_chunk = 0;
+        pst = unbalanced_plan(ctx, m, nb, s, &chunk_slot, &ops_chunk);
+        if (pst != GF2X_OK)
+            return pst;
+        if ((uint64_t)k * ops_chunk < ops_pad) {
+            size = m;
+            chunks = k;
+            Ld = Lc;
+            step = Lc;
+            slot = chunk_slot;
+        }
+    }
+    const uint32_t Wp = (uint32_t)((2ull * size - 1 + 63) / 64);
+    if (chunks == 1)
+        step = Wp;
+    // scratch per product: chunks x (two operand rows + one product row)
+    const size_t per = 8ull * chunks * (2ull * Ld + Wp);
+    const size_t group = std::max<size_t>(1, std::min<size_t>(count, kWorkspaceCap / per));
+    const size_t want = group * per;
+    if (ctx->ub_bytes < want) {
+        if (ctx->ub) {
+            cudaError_t e = cudaFree(ctx->ub);   // synchronizes the device: no call still uses it
+            ctx->ub = nullptr;
+            ctx->ub_bytes = 0;
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e, "unbalanced scratch");
+        }
+        cudaError_t e = cudaMalloc((void **)&ctx->ub, want);
+        if (e != cudaSuccess) {
+            ctx->ub = nullptr;
+            return e == cudaErrorMemoryAllocation ? fail(ctx, GF2X_ENOMEM, "unbalanced scratch")
+                                                  : cuda_fail(ctx, e, "unbalanced scratch");
+        }
+        ctx->ub_bytes = want;
+    }
+    if (!ctx->ub_done) {
+        cudaError_t e = cudaEventCreateWithFlags(&ctx->ub_done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            ctx->ub_done = nullptr;
+            return cuda_fail(ctx, e, "unbalanced scratch event");
+        }
+    }
+    // the scratch is shared by every call of the context: order this call
+    // after the previous one when that came on another stream
+    if (ctx->ub_used && ctx->ub_stream != s) {
+        cudaError_t e = cudaStreamWaitEvent(s, ctx->ub_done, 0);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "unbalanced scratch ordering");
+    }
+    for (size_t c0 = 0; c0 < count; c0 += group) {
+        const size_t g = std::min(group, count - c0);
+        uint64_t *A = ctx->ub, *B = A + g * chunks * Ld, *P = B + g * chunks * Ld;
+        cudaError_t e = launch_pad_rows(A, a + c0 * stride_a, stride_a, na, g, chunks, Ld, chunks > 1 ? Lc : 0u,
+                                        ctx->sm_count, s);
+        if (e == cudaSuccess)
+            e = launch_pad_rows(B, b + c0 * stride_b, stride_b, nb, g, chunks, Ld, 0u, ctx->sm_count, s);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "operand padding launch");
+        if (g * chunks > 0xffffffffull)
+            return fail(ctx, GF2X_EINVAL, "batch too large");
+        gf2x_status st = strided_on_slot(ctx, slot, P, A, B, g * chunks, Ld, Wp, 0u, GF2X_BATCH_PERSISTENT, s);
+        if (st != GF2X_OK)
+            return st;
+        e = launch_overlap_add(out + c0 * stride_out, stride_out, Lu, P, Wp, g, chunks, step, ctx->sm_count, s);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "overlap-add launch");
+    }
+    cudaError_t e = cudaEventRecord(ctx->ub_done, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "unbalanced scratch event");
+    ctx->ub_used = true;
+    ctx->ub_stream = s;
+    return GF2X_OK;
 }
 
 // k rows of `width` limbs, `dpitch` / `spitch` limbs apart.

@@ -22,6 +22,12 @@ cudaError_t launch_split_interp(const LaunchArgs &a, const uint32_t *scratch, un
                                 size_t smem, cudaStream_t st);
 cudaError_t prepare_split();
 
+// operands of different sizes (unbalanced.cu)
+cudaError_t launch_pad_rows(uint64_t *dst, const uint64_t *src, size_t stride_src, uint32_t nsrc, size_t count,
+                            uint32_t k, uint32_t Ld, uint32_t step, int sm_count, cudaStream_t st);
+cudaError_t launch_overlap_add(uint64_t *out, size_t stride_out, uint32_t Lu, const uint64_t *prod, uint32_t Wp,
+                               size_t count, uint32_t k, uint32_t step, int sm_count, cudaStream_t st);
+
 typedef cudaError_t (*LaunchFn)(const LaunchArgs &, unsigned, unsigned, size_t, cudaStream_t);
 typedef cudaError_t (*PrepareFn)(int *, unsigned, size_t);
 

@@ -80,6 +80,7 @@ _SIGNATURES = {
     "gf2x_mulmod_xn1": ([_P, _P, _P, _P, _U32, _P], _I),
     "gf2x_mul_strided": ([_P, _P, _P, _P, _U32, _SZ, _SZ, _SZ, _U32, _U32, _P], _I),
     "gf2x_mul_strided_host": ([_P, _P, _P, _P, _U32, _SZ, _SZ, _SZ, _U32, _P], _I),
+    "gf2x_mul_unbalanced": ([_P, _P, _P, _U32, _SZ, _P, _U32, _SZ, _SZ, _SZ, _P], _I),
     "gf2x_mul_batched": ([_P, _P, _SZ, _U32, _P], _I),
     "gf2x_ctx_prepare": ([_P, ctypes.POINTER(_U32), _SZ, _P], _I),
     "gf2x_ctx_launch_shape": ([_P, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32),
@@ -282,6 +283,28 @@ class Context:
                                            b.shape[1], out.shape[1], REDUCE if reduce else 0,
                                            bflags, _stream_handle(stream)),
                     "gf2x_mul_strided")
+        return out
+
+    def mul_unbalanced(self, a: torch.Tensor, na: int, b: torch.Tensor, nb: int, out: torch.Tensor | None = None,
+                       stream=None):
+        """Full products of operands of different sizes: rows of a (na bits)
+        times rows of b (nb bits), each 1-D (one product) or 2-D (one per
+        row); result rows of ceil((na + nb - 1)/64) limbs."""
+        if a.dim() != b.dim() or a.dim() not in (1, 2) or (a.dim() == 2 and a.shape[0] != b.shape[0]):
+            raise ValueError("a and b must both be 1-D, or 2-D with the same number of rows")
+        _check_operand(a, na, "a")
+        _check_operand(b, nb, "b")
+        one = a.dim() == 1
+        A, B = (a[None], b[None]) if one else (a, b)
+        count, ol = A.shape[0], (na + nb - 1 + 63) // 64
+        if out is None:
+            out = torch.empty((ol,) if one else (count, ol), dtype=torch.int64, device=a.device)
+        O = out[None] if out.dim() == 1 else out
+        if O.dim() != 2 or O.shape[0] != count or O.shape[1] < ol or not O.is_contiguous():
+            raise ValueError("bad output tensor")
+        self._raise(lib().gf2x_mul_unbalanced(self._h, O.data_ptr(), A.data_ptr(), na, A.shape[1], B.data_ptr(), nb,
+                                              B.shape[1], count, O.shape[1], _stream_handle(stream)),
+                    "gf2x_mul_unbalanced")
         return out
 
     def mul_strided_host(self, a: torch.Tensor, b: torch.Tensor, n: int, reduce: bool,
