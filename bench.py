@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="hqc128")
     p.add_argument("--no-plain", action="store_true", help="skip the plain one-launch-per-product measurement")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle cpu_baseline sample")
-    p.add_argument("--no-extras", action="store_true", help="skip the other workloads (C1, C3, C4, shared key, unbalanced, C5)")
+    p.add_argument("--no-extras", action="store_true", help="skip the other workloads (C1, C3, C4, shared key, unbalanced, sparse, C5)")
     p.add_argument("--serving-requests", type=int, default=200000)
     p.add_argument("--plan", default=None, help="plan spec for the main workload (default: the tuned database)")
     return p.parse_args()
@@ -760,6 +760,51 @@ def run_unbalanced(device):
             "sample_checked_against_oracle": ok}
 
 
+def run_sparse(device):
+    """Constant-time sparse x dense products mod X^n - 1 (HQC shapes: n =
+    17669 with weight 75, n = 57637 with weight 131) against the dense path
+    on the same operands (the sparse operand expanded to n bits)."""
+    import torch
+
+    import oracle
+    from paper_2201_10473_gb300 import Context
+    res = {}
+    for n, w, count in ((17669, 75, 4096), (57637, 131, 2048)):
+        ctx = Context(device, batch_hint=count)
+        rows = wl.sparse_operands(wl.BASE_SEED + 10, n, w, count)
+        pos = np.stack([np.flatnonzero(np.unpackbits(r.view(np.uint8), bitorder="little"))[:w] for r in rows])
+        R = 4
+        da = [_dev(wl.dense_operands(wl.BASE_SEED + 10, n, count, 0, first=r * count)) for r in range(R)]
+        dpos, dden = torch.from_numpy(pos.astype(np.int32)).cuda(), _dev(rows)
+        out = torch.empty((count, wl.limbs(n)), dtype=torch.int64, device="cuda")
+        it = [0]
+
+        def sparse():
+            ctx.mulmod_sparse(da[it[0] % R], dpos, n, out=out)
+            it[0] += 1
+
+        def dense():
+            ctx.mul_strided(da[it[0] % R], dden, n, True, out=out, persistent=True)
+            it[0] += 1
+        rates = {}
+        for rep in range(2):
+            for name, fn in (("sparse", sparse), ("dense", dense)):
+                it[0] = 0
+                ms = _time_calls(fn, 10, 3)
+                rates.setdefault(name, []).append(count / (ms * 1e-3))
+        it[0] = 0
+        sparse()
+        a0 = _host(da[0])
+        got = _host(out)
+        ok = all(np.array_equal(got[p], oracle.mulmod(a0[p], rows[p], n)) for p in range(0, count, 512))
+        ctx.close()
+        sp, de = max(rates["sparse"]), max(rates["dense"])
+        res[f"n{n}_w{w}"] = {"products": count, "sparse_mults_per_s": sp, "dense_path_mults_per_s": de,
+                             "sparse_over_dense": sp / de, "sample_checked_against_oracle": ok}
+    res["workload"] = "hqc-sparse-times-dense-mulmod"
+    return res
+
+
 def run_c5(device, requests):
     """Serving: Poisson arrivals, HBM-budget admission, continuous batching."""
     import torch  # noqa: F401
@@ -844,6 +889,7 @@ def run_extras(args, device):
     res = {}
     for name, fn in (("c1", lambda: run_c1(device)), ("c3", lambda: run_c3(device)), ("c4", lambda: run_c4(device)),
                      ("shared_key", lambda: run_shared(device)), ("unbalanced", lambda: run_unbalanced(device)),
+                     ("sparse_ct", lambda: run_sparse(device)),
                      ("c5", lambda: run_c5(device, args.serving_requests))):
         t0 = time.time()
         try:

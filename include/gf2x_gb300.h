@@ -281,6 +281,27 @@ gf2x_status gf2x_mul_unbalanced(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a,
                                 const uint64_t *b, uint32_t nb, size_t stride_b, size_t count, size_t stride_out,
                                 gf2x_stream stream);
 
+/* Constant-time products of a dense a and a sparse b mod X^n - 1, the
+ * operand shape of the HQC/BIKE operations of Sec. 1 (a public dense
+ * polynomial times a secret low-weight one).  b = sum_j X^(pos[j]) over its w
+ * positions (repeated positions cancel, as in F2); result row p = a_p * b_p
+ * mod X^n - 1 in ceil(n/64) limbs, bits above n zero.  Sec. 1 rules out
+ * multiplications that use the sparsity through branches or memory
+ * addresses; this one never does: each position becomes the masks of a
+ * barrel shifter and the count of a funnel shift on the doubled vector
+ * a + X^n a, so the work and the addresses depend on n, w and count only.
+ *  - a: count rows of ceil(n/64) limbs, stride_a limbs apart (bits above n
+ *    ignored); pos: count rows of w uint32 positions, stride_pos entries
+ *    apart, each < n (a position >= n gives an unspecified row, never an
+ *    access outside the operands); r: count rows, stride_r limbs apart.
+ *  - One warp per product, one launch on `stream`; n up to 65536.
+ *  - Errors: GF2X_EUNSUPPORTED for n outside [1, 65536]; GF2X_EINVAL for
+ *    null or misaligned pointers (8 bytes for a and r, 4 for pos), short
+ *    strides, results overlapping a or pos. */
+gf2x_status gf2x_mulmod_sparse(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a, const uint32_t *pos, uint32_t w,
+                               uint32_t n, size_t count, size_t stride_a, size_t stride_pos, size_t stride_r,
+                               gf2x_stream stream);
+
 /* Build and upload (synchronously on `stream`) the current plans of the
  * given sizes, so that later calls and CUDA graph captures find them ready,
  * and make exactly these sizes the ones device-item batches accept (their

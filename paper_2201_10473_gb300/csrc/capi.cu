@@ -814,6 +814,53 @@ extern "C" gf2x_status gf2x_mul_unbalanced(gf2x_ctx *ctx, uint64_t *out, const u
     return GF2X_OK;
 }
 
+extern "C" gf2x_status gf2x_mulmod_sparse(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a, const uint32_t *pos,
+                                          uint32_t w, uint32_t n, size_t count, size_t stride_a, size_t stride_pos,
+                                          size_t stride_r, gf2x_stream stream)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    if (count == 0)
+        return GF2X_OK;
+    if (n < 1 || n > kSparseMaxN)
+        return fail(ctx, GF2X_EUNSUPPORTED, "n outside [1, 65536] for the sparse product");
+    if (!r || !a || (w && !pos))
+        return fail(ctx, GF2X_EINVAL, "null operand or result pointer");
+    if ((((uintptr_t)r | (uintptr_t)a) & 7u) || ((uintptr_t)pos & 3u))
+        return fail(ctx, GF2X_EINVAL, "misaligned operand or result");
+    const size_t L = (n + 63) / 64;
+    if (count > 1 && (stride_a < L || stride_r < L || stride_pos < w))
+        return fail(ctx, GF2X_EINVAL, "stride smaller than the operand, position list or result");
+    if (count > 0xffffffffull)
+        return fail(ctx, GF2X_EINVAL, "batch too large");
+    const size_t r_bytes = 8 * ((count - 1) * stride_r + L);
+    if (ranges_overlap(r, r_bytes, a, 8 * ((count - 1) * stride_a + L)) ||
+        (w && ranges_overlap(r, r_bytes, pos, 4 * ((count - 1) * stride_pos + w))))
+        return fail(ctx, GF2X_EINVAL, "result overlaps an operand");
+    SparseShape sh;
+    if (!sparse_shape(n, &sh))
+        return fail(ctx, GF2X_EUNSUPPORTED, "no sparse kernel shape for this n");
+    SparseArgs args;
+    memset(&args, 0, sizeof(args));
+    args.a = a;
+    args.pos = pos;
+    args.r = r;
+    args.stride_a = stride_a;
+    args.stride_pos = stride_pos;
+    args.stride_r = stride_r;
+    args.n = n;
+    args.w = w;
+    args.count = (uint32_t)count;
+    args.stages = sh.T - sh.pre;
+    args.pre = sh.pre;
+    args.d_words = sh.d_words;
+    args.b_words = sh.b_words;
+    cudaError_t e = launch_sparse_mulmod(args, sh, ctx->sm_count, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "sparse product launch");
+    return GF2X_OK;
+}
+
 // k rows of `width` limbs, `dpitch` / `spitch` limbs apart.
 static cudaError_t copy_rows(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, size_t k,
                              cudaMemcpyKind kind, cudaStream_t st)

@@ -28,6 +28,27 @@ cudaError_t launch_pad_rows(uint64_t *dst, const uint64_t *src, size_t stride_sr
 cudaError_t launch_overlap_add(uint64_t *out, size_t stride_out, uint32_t Lu, const uint64_t *prod, uint32_t Wp,
                                size_t count, uint32_t k, uint32_t step, int sm_count, cudaStream_t st);
 
+// constant-time sparse x dense product mod X^n - 1 (sparse.cu)
+constexpr uint32_t kSparseMaxN = 65536;
+struct SparseArgs {
+    const uint64_t *a;        // dense rows, ceil(n/64) limbs, stride_a limbs apart
+    const uint32_t *pos;      // w positions per product, stride_pos entries apart
+    uint64_t *r;              // result rows, ceil(n/64) limbs, stride_r limbs apart
+    size_t stride_a, stride_pos, stride_r;
+    uint32_t n, w, count;
+    uint32_t stages;          // barrel stages in registers
+    uint32_t pre;             // largest stages in shared memory first (staged variant)
+    uint32_t d_words, b_words; // shared words per warp: doubled vector, stage buffer
+};
+struct SparseShape {
+    uint32_t N, T;            // words of a, bits of the largest word offset n/32
+    uint32_t C;               // window words per lane
+    uint32_t staged, pre, d_words, b_words;
+};
+bool sparse_shape(uint32_t n, SparseShape *sh);
+size_t sparse_smem_bytes(const SparseShape &sh);
+cudaError_t launch_sparse_mulmod(const SparseArgs &args, const SparseShape &sh, int sm_count, cudaStream_t st);
+
 typedef cudaError_t (*LaunchFn)(const LaunchArgs &, unsigned, unsigned, size_t, cudaStream_t);
 typedef cudaError_t (*PrepareFn)(int *, unsigned, size_t);
 

@@ -1,0 +1,281 @@
+// sparse.cu -- constant-time product of a dense a and a sparse b given by
+// its w set positions, modulo X^n - 1: the operand shape of the HQC and BIKE
+// operations of Sec. 1, where the sparse operand is secret.  Sec. 1 rules
+// out methods that use the sparsity through branches or addresses; here the
+// positions only enter masks and shift counts:
+//   r = sum_j X^(p_j) a mod (X^n - 1) = sum_j rot(a, p_j),
+// and rot(a, p) is the n-bit window at bit s = n - p of D = a + X^n a (the
+// doubled vector, 2n bits).  The window's word offset q = s >> 5 is applied
+// by a barrel shifter (stage t moves every word by 2^t under the mask of bit
+// t of q, both candidates read, no secret address), its bit offset s & 31 by
+// a funnel shift (constant time in the shift count), and the windows are
+// XORed into the accumulator.
+//
+// One warp per product.  Word i = lane C + k of the cyclic window lives in
+// register k of lane `lane` (C words per lane, 32 C >= the window); a shift
+// by 2^t words is a register rename plus __shfl_sync from a fixed lane
+// offset.  Small n keep D itself in registers; larger n first apply the
+// largest shifts in shared memory, shrinking the window to what the
+// register stages need.  Work per product: w x (stages x C) selects and
+// shuffles per lane, independent of the operand bits.
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "launchers.h"
+
+namespace gf2x {
+
+constexpr int kSparseWarps = 4;
+constexpr int kSparseMaxStages = 12;   // q < 2^12 words covers n <= 131072
+
+// Cyclic shift of the 32 C-word window held by the warp: afterwards word w
+// is the former word (w + q mod 2^stages) mod 32C, stage t taken under the
+// mask of bit t of q (stages is uniform over the warp).
+template <int C>
+__device__ __forceinline__ void barrel(uint32_t (&y)[C], uint32_t q, uint32_t stages, uint32_t lane)
+{
+#pragma unroll
+    for (int t = 0; t < kSparseMaxStages; ++t) {
+        if ((uint32_t)t < stages) {
+            const uint32_t m = 0u - ((q >> t) & 1u);
+            uint32_t nv[C];
+#pragma unroll
+            for (int k = 0; k < C; ++k) {
+                const int g = k + (1 << t);
+                const int d = g / C, kk = g % C;
+                const uint32_t v = (d % 32 == 0) ? y[kk] : __shfl_sync(0xffffffffu, y[kk], (lane + d) & 31u);
+                nv[k] = (v & m) | (y[k] & ~m);
+            }
+#pragma unroll
+            for (int k = 0; k < C; ++k)
+                y[k] = nv[k];
+        }
+    }
+}
+
+// acc ^= the n-bit window at bit offset b of the window held in y (word w of
+// the result = bits [32w + b, 32w + b + 32) of y).
+template <int C>
+__device__ __forceinline__ void add_window(uint32_t (&acc)[C], const uint32_t (&y)[C], uint32_t b, uint32_t lane)
+{
+    const uint32_t next = __shfl_sync(0xffffffffu, y[0], (lane + 1u) & 31u);
+#pragma unroll
+    for (int k = 0; k < C; ++k)
+        acc[k] ^= __funnelshift_r(y[k], k + 1 < C ? y[k + 1] : next, b);
+}
+
+// D = a + X^n a into `dst` (len words, zero past 2n bits); a masked to n bits.
+__device__ __forceinline__ void build_doubled(uint32_t *dst, uint32_t len, const uint32_t *a32, uint32_t n,
+                                              uint32_t lane)
+{
+    const uint32_t N = (n + 31u) / 32u, q0 = n >> 5, r0 = n & 31u;
+    const uint32_t top = r0 ? (1u << r0) - 1u : 0xffffffffu;
+    for (uint32_t w = lane; w < len; w += 32u) {
+        uint32_t v = 0;
+        if (w < N)
+            v = a32[w] & (w == N - 1u ? top : 0xffffffffu);
+        if (w >= q0 && w - q0 <= N) {
+            const uint32_t i = w - q0;
+            const uint32_t x = i < N ? a32[i] & (i == N - 1u ? top : 0xffffffffu) : 0u;
+            const uint32_t xp = (i >= 1u && i - 1u < N) ? a32[i - 1u] & (i - 1u == N - 1u ? top : 0xffffffffu) : 0u;
+            v |= r0 ? (x << r0) | (xp >> (32u - r0)) : x;
+        }
+        dst[w] = v;
+    }
+}
+
+template <int C>
+__device__ __forceinline__ void store_result(uint64_t *r_row, const uint32_t (&acc)[C], uint32_t n, uint32_t lane)
+{
+    const uint32_t N = (n + 31u) / 32u, words = 2u * ((n + 63u) / 64u);
+    const uint32_t top = (n & 31u) ? (1u << (n & 31u)) - 1u : 0xffffffffu;
+    uint32_t *r32 = reinterpret_cast<uint32_t *>(r_row);
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        const uint32_t w = lane * C + k;
+        if (w < words)
+            r32[w] = w < N ? acc[k] & (w == N - 1u ? top : 0xffffffffu) : 0u;
+    }
+}
+
+// Small n (32 C >= N + n/32 + 1): D stays in registers (dreg), every
+// position runs all its stages there.
+template <int C>
+__global__ void __launch_bounds__(32 * kSparseWarps) sparse_mulmod_regs_kernel(const SparseArgs args)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t *D = smem + warp * (32u * C);
+    const uint32_t step = gridDim.x * kSparseWarps;
+    for (uint32_t p = blockIdx.x * kSparseWarps + warp; p < args.count; p += step) {
+        const uint32_t *a32 = reinterpret_cast<const uint32_t *>(args.a + (size_t)p * args.stride_a);
+        const uint32_t *pos = args.pos + (size_t)p * args.stride_pos;
+        build_doubled(D, 32u * C, a32, args.n, lane);
+        __syncwarp();
+        uint32_t dreg[C], acc[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            dreg[k] = D[lane * C + k];
+            acc[k] = 0u;
+        }
+        __syncwarp();
+        for (uint32_t j0 = 0; j0 < args.w; j0 += 32u) {
+            const uint32_t mine = j0 + lane < args.w ? pos[j0 + lane] : 0u;
+            const uint32_t cnt = args.w - j0 < 32u ? args.w - j0 : 32u;
+            for (uint32_t jj = 0; jj < cnt; ++jj) {
+                const uint32_t s = args.n - __shfl_sync(0xffffffffu, mine, jj);
+                uint32_t y[C];
+#pragma unroll
+                for (int k = 0; k < C; ++k)
+                    y[k] = dreg[k];
+                barrel<C>(y, s >> 5, args.stages, lane);
+                add_window<C>(acc, y, s & 31u, lane);
+            }
+        }
+        store_result<C>(args.r + (size_t)p * args.stride_r, acc, args.n, lane);
+    }
+}
+
+// Larger n: D in shared memory; the `pre` largest shifts run there (the
+// first from D into B, the rest in place in B), then the register window
+// (32 C words of B, or of D when pre = 0) takes the remaining stages.
+template <int C>
+__global__ void __launch_bounds__(32 * kSparseWarps) sparse_mulmod_staged_kernel(const SparseArgs args)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t *D = smem + warp * (args.d_words + args.b_words);
+    uint32_t *B = D + args.d_words;
+    const uint32_t N = (args.n + 31u) / 32u;
+    const uint32_t step = gridDim.x * kSparseWarps;
+    for (uint32_t p = blockIdx.x * kSparseWarps + warp; p < args.count; p += step) {
+        const uint32_t *a32 = reinterpret_cast<const uint32_t *>(args.a + (size_t)p * args.stride_a);
+        const uint32_t *pos = args.pos + (size_t)p * args.stride_pos;
+        build_doubled(D, args.d_words, a32, args.n, lane);
+        __syncwarp();
+        uint32_t acc[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k)
+            acc[k] = 0u;
+        const uint32_t *src = args.pre ? B : D;
+        for (uint32_t j0 = 0; j0 < args.w; j0 += 32u) {
+            const uint32_t mine = j0 + lane < args.w ? pos[j0 + lane] : 0u;
+            const uint32_t cnt = args.w - j0 < 32u ? args.w - j0 : 32u;
+            for (uint32_t jj = 0; jj < cnt; ++jj) {
+                const uint32_t s = args.n - __shfl_sync(0xffffffffu, mine, jj);
+                const uint32_t q = s >> 5;
+                for (uint32_t u = 0; u < args.pre; ++u) {
+                    const uint32_t t = args.stages + args.pre - 1u - u;   // largest first
+                    const uint32_t sh = 1u << t, m = 0u - ((q >> t) & 1u);
+                    const uint32_t len = N + sh;     // what the smaller shifts still need
+                    const uint32_t *in = u == 0 ? D : B;
+                    // uniform trip count: every lane reaches each __syncwarp
+                    for (uint32_t w0 = 0; w0 < len; w0 += 32u) {
+                        const uint32_t w = w0 + lane;
+                        uint32_t v = 0;
+                        if (w < len)
+                            v = (in[w + sh] & m) | (in[w] & ~m);
+                        __syncwarp();
+                        if (w < len)
+                            B[w] = v;
+                    }
+                    __syncwarp();
+                }
+                uint32_t y[C];
+#pragma unroll
+                for (int k = 0; k < C; ++k)
+                    y[k] = src[lane * C + k];
+                __syncwarp();   // B is rewritten by the next position's first stage
+                barrel<C>(y, q, args.stages, lane);
+                add_window<C>(acc, y, s & 31u, lane);
+            }
+        }
+        store_result<C>(args.r + (size_t)p * args.stride_r, acc, args.n, lane);
+    }
+}
+
+template <int C>
+static cudaError_t launch_regs(const SparseArgs &a, unsigned grid, cudaStream_t st)
+{
+    const size_t smem = 4ull * kSparseWarps * 32u * C;
+    sparse_mulmod_regs_kernel<C><<<grid, 32 * kSparseWarps, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int C>
+static cudaError_t launch_staged(const SparseArgs &a, unsigned grid, cudaStream_t st)
+{
+    const size_t smem = 4ull * kSparseWarps * (a.d_words + a.b_words);
+    cudaError_t e = cudaFuncSetAttribute(sparse_mulmod_staged_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    sparse_mulmod_staged_kernel<C><<<grid, 32 * kSparseWarps, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Window sizes C (words per lane) of the compiled variants.
+constexpr int kRegsC[] = {9, 17, 35};
+constexpr int kStagedC = 73;
+
+bool sparse_shape(uint32_t n, SparseShape *sh)
+{
+    if (n < 1 || n > kSparseMaxN)
+        return false;
+    const uint32_t N = (n + 31u) / 32u, qmax = n >> 5;
+    uint32_t T = 0;
+    while (T < 32u && (qmax >> T) != 0u)
+        ++T;
+    sh->N = N;
+    sh->T = T;
+    for (int C : kRegsC) {
+        if (32u * (uint32_t)C >= N + qmax + 1u) {
+            sh->C = (uint32_t)C;
+            sh->staged = 0;
+            sh->pre = 0;
+            sh->d_words = 0;
+            sh->b_words = 0;
+            return true;
+        }
+    }
+    const uint32_t M = 32u * kStagedC;
+    for (uint32_t pre = 0; pre <= T; ++pre) {
+        // after the pre largest shifts the remaining offset is below 2^(T - pre)
+        const uint32_t need = pre == 0 ? N + qmax + 1u : N + (1u << (T - pre));
+        if (need <= M) {
+            sh->C = kStagedC;
+            sh->staged = 1;
+            sh->pre = pre;
+            sh->d_words = pre == 0 ? M : (N + (1u << T) > M ? N + (1u << T) : M);
+            sh->b_words = pre == 0 ? 0u : (N + (1u << (T - 1u)) > M ? N + (1u << (T - 1u)) : M);
+            return true;
+        }
+    }
+    return false;
+}
+
+size_t sparse_smem_bytes(const SparseShape &sh)
+{
+    return sh.staged ? 4ull * kSparseWarps * (sh.d_words + sh.b_words) : 4ull * kSparseWarps * 32u * sh.C;
+}
+
+cudaError_t launch_sparse_mulmod(const SparseArgs &args, const SparseShape &sh, int sm_count, cudaStream_t st)
+{
+    const size_t ctas = (args.count + kSparseWarps - 1) / kSparseWarps;
+    const size_t cap = (size_t)(sm_count > 0 ? sm_count : 1) * 8u;
+    const unsigned grid = (unsigned)(ctas < cap ? ctas : cap);
+    if (grid == 0)
+        return cudaSuccess;
+    if (!sh.staged) {
+        switch (sh.C) {
+        case 9: return launch_regs<9>(args, grid, st);
+        case 17: return launch_regs<17>(args, grid, st);
+        case 35: return launch_regs<35>(args, grid, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    return sh.C == kStagedC ? launch_staged<kStagedC>(args, grid, st) : cudaErrorInvalidValue;
+}
+
+}  // namespace gf2x

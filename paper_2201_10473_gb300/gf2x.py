@@ -81,6 +81,7 @@ _SIGNATURES = {
     "gf2x_mul_strided": ([_P, _P, _P, _P, _U32, _SZ, _SZ, _SZ, _U32, _U32, _P], _I),
     "gf2x_mul_strided_host": ([_P, _P, _P, _P, _U32, _SZ, _SZ, _SZ, _U32, _P], _I),
     "gf2x_mul_unbalanced": ([_P, _P, _P, _U32, _SZ, _P, _U32, _SZ, _SZ, _SZ, _P], _I),
+    "gf2x_mulmod_sparse": ([_P, _P, _P, _P, _U32, _U32, _SZ, _SZ, _SZ, _SZ, _P], _I),
     "gf2x_mul_batched": ([_P, _P, _SZ, _U32, _P], _I),
     "gf2x_ctx_prepare": ([_P, ctypes.POINTER(_U32), _SZ, _P], _I),
     "gf2x_ctx_launch_shape": ([_P, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32),
@@ -305,6 +306,26 @@ class Context:
         self._raise(lib().gf2x_mul_unbalanced(self._h, O.data_ptr(), A.data_ptr(), na, A.shape[1], B.data_ptr(), nb,
                                               B.shape[1], count, O.shape[1], _stream_handle(stream)),
                     "gf2x_mul_unbalanced")
+        return out
+
+    def mulmod_sparse(self, a: torch.Tensor, pos: torch.Tensor, n: int, out: torch.Tensor | None = None,
+                      stream=None):
+        """Constant-time a * b mod X^n - 1 with b = sum_j X^pos[j]: a is a
+        (count, >= ceil(n/64)) int64 CUDA tensor of dense rows, pos a
+        (count, w) int32 CUDA tensor of positions (< n) of the sparse rows."""
+        if a.dim() != 2 or pos.dim() != 2 or pos.shape[0] != a.shape[0]:
+            raise ValueError("a and pos must be 2-D with one row per product")
+        _check_operand(a, n, "a")
+        if pos.dtype != torch.int32 or not pos.is_cuda or not pos.is_contiguous():
+            raise TypeError("pos must be a contiguous CUDA int32 tensor")
+        count, w = a.shape[0], pos.shape[1]
+        if out is None:
+            out = torch.empty((count, limbs(n)), dtype=torch.int64, device=a.device)
+        if out.dim() != 2 or out.shape[0] != count or out.shape[1] < limbs(n) or not out.is_contiguous():
+            raise ValueError("bad output tensor")
+        self._raise(lib().gf2x_mulmod_sparse(self._h, out.data_ptr(), a.data_ptr(), pos.data_ptr() if w else None,
+                                             w, n, count, a.shape[1], w, out.shape[1], _stream_handle(stream)),
+                    "gf2x_mulmod_sparse")
         return out
 
     def mul_strided_host(self, a: torch.Tensor, b: torch.Tensor, n: int, reduce: bool,
