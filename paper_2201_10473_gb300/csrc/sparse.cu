@@ -102,7 +102,7 @@ __device__ __forceinline__ void store_result(uint64_t *r_row, const uint32_t (&a
 // Small n (32 C >= N + n/32 + 1): D stays in registers (dreg), every
 // position runs all its stages there.
 template <int C>
-__global__ void __launch_bounds__(32 * kSparseWarps) sparse_mulmod_regs_kernel(const SparseArgs args)
+__global__ void __launch_bounds__(32 * kSparseWarps, 3) sparse_mulmod_regs_kernel(const SparseArgs args)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -170,15 +170,24 @@ __global__ void __launch_bounds__(32 * kSparseWarps) sparse_mulmod_staged_kernel
                     const uint32_t sh = 1u << t, m = 0u - ((q >> t) & 1u);
                     const uint32_t len = N + sh;     // what the smaller shifts still need
                     const uint32_t *in = u == 0 ? D : B;
-                    // uniform trip count: every lane reaches each __syncwarp
-                    for (uint32_t w0 = 0; w0 < len; w0 += 32u) {
-                        const uint32_t w = w0 + lane;
-                        uint32_t v = 0;
-                        if (w < len)
-                            v = (in[w + sh] & m) | (in[w] & ~m);
+                    // in place: 256 words are read before any is written,
+                    // and sh >= 256 (sparse_shape) keeps every read ahead of
+                    // the writes; uniform trip count, every lane reaches
+                    // each __syncwarp
+                    for (uint32_t w0 = 0; w0 < len; w0 += 256u) {
+                        uint32_t v[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const uint32_t w = w0 + 32u * e + lane;
+                            v[e] = w < len ? (in[w + sh] & m) | (in[w] & ~m) : 0u;
+                        }
                         __syncwarp();
-                        if (w < len)
-                            B[w] = v;
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const uint32_t w = w0 + 32u * e + lane;
+                            if (w < len)
+                                B[w] = v[e];
+                        }
                     }
                     __syncwarp();
                 }
@@ -244,6 +253,9 @@ bool sparse_shape(uint32_t n, SparseShape *sh)
         // after the pre largest shifts the remaining offset is below 2^(T - pre)
         const uint32_t need = pre == 0 ? N + qmax + 1u : N + (1u << (T - pre));
         if (need <= M) {
+            // the in-place shared stages read 256 words ahead of their writes
+            if (pre > 0 && (1u << (T - pre)) < 256u)
+                return false;
             sh->C = kStagedC;
             sh->staged = 1;
             sh->pre = pre;
