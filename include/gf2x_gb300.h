@@ -294,7 +294,8 @@ gf2x_status gf2x_mul_unbalanced(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a,
  *    ignored); pos: count rows of w uint32 positions, stride_pos entries
  *    apart, each < n (a position >= n gives an unspecified row, never an
  *    access outside the operands); r: count rows, stride_r limbs apart.
- *  - One warp per product, one launch on `stream`; n up to 65536.
+ *  - One CTA per product (its four warps share the positions), one launch
+ *    on `stream`; n up to 65536.
  *  - Errors: GF2X_EUNSUPPORTED for n outside [1, 65536]; GF2X_EINVAL for
  *    null or misaligned pointers (8 bytes for a and r, 4 for pos), short
  *    strides, results overlapping a or pos. */

@@ -11,13 +11,15 @@
 // a funnel shift (constant time in the shift count), and the windows are
 // XORed into the accumulator.
 //
-// One warp per product.  Word i = lane C + k of the cyclic window lives in
-// register k of lane `lane` (C words per lane, 32 C >= the window); a shift
-// by 2^t words is a register rename plus __shfl_sync from a fixed lane
-// offset.  Small n keep D itself in registers; larger n first apply the
-// largest shifts in shared memory, shrinking the window to what the
-// register stages need.  Work per product: w x (stages x C) selects and
-// shuffles per lane, independent of the operand bits.
+// One CTA per product; each of its four warps takes a quarter of the
+// positions, and the four partial sums are XORed at the end.  Word
+// i = lane C + k of a warp's cyclic window lives in register k of lane
+// `lane` (C words per lane, 32 C >= the window); a shift by 2^t words is a
+// register rename plus __shfl_sync from a fixed lane offset.  Small n keep D
+// itself in registers; larger n first apply the largest shifts in shared
+// memory, shrinking the window to what the register stages need.  Work per
+// product: w x (stages x C) selects and shuffles per lane, independent of
+// the operand bits.
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -67,11 +69,11 @@ __device__ __forceinline__ void add_window(uint32_t (&acc)[C], const uint32_t (&
 
 // D = a + X^n a into `dst` (len words, zero past 2n bits); a masked to n bits.
 __device__ __forceinline__ void build_doubled(uint32_t *dst, uint32_t len, const uint32_t *a32, uint32_t n,
-                                              uint32_t lane)
+                                              uint32_t first, uint32_t stride)
 {
     const uint32_t N = (n + 31u) / 32u, q0 = n >> 5, r0 = n & 31u;
     const uint32_t top = r0 ? (1u << r0) - 1u : 0xffffffffu;
-    for (uint32_t w = lane; w < len; w += 32u) {
+    for (uint32_t w = first; w < len; w += stride) {
         uint32_t v = 0;
         if (w < N)
             v = a32[w] & (w == N - 1u ? top : 0xffffffffu);
@@ -99,30 +101,65 @@ __device__ __forceinline__ void store_result(uint64_t *r_row, const uint32_t (&a
     }
 }
 
-// Small n (32 C >= N + n/32 + 1): D stays in registers (dreg), every
-// position runs all its stages there.
+// The positions of product p that warp `warp` of its CTA takes: an equal
+// share of the w (sizes only; the CTA's four partial sums are XORed).
+__device__ __forceinline__ void warp_share(uint32_t w, uint32_t warp, uint32_t *jb, uint32_t *je)
+{
+    *jb = (uint32_t)(((uint64_t)w * warp) / kSparseWarps);
+    *je = (uint32_t)(((uint64_t)w * (warp + 1u)) / kSparseWarps);
+}
+
+// The CTA's four partial sums into warp 0's acc (red: three buffers of
+// 32 C words, one per other warp), then warp 0 stores the row.
+template <int C>
+__device__ __forceinline__ void reduce_and_store(uint32_t (&acc)[C], uint32_t *red, size_t red_stride,
+                                                 uint64_t *r_row, uint32_t n, uint32_t lane, uint32_t warp)
+{
+    if (warp > 0) {
+        uint32_t *mine = red + (warp - 1u) * red_stride;
+#pragma unroll
+        for (int k = 0; k < C; ++k)
+            mine[lane * C + k] = acc[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (uint32_t g = 0; g + 1u < (uint32_t)kSparseWarps; ++g) {
+#pragma unroll
+            for (int k = 0; k < C; ++k)
+                acc[k] ^= red[g * red_stride + lane * C + k];
+        }
+        store_result<C>(r_row, acc, n, lane);
+    }
+}
+
+// One CTA per product (persistent over the batch), its four warps each
+// taking a quarter of the positions.  Small n (32 C >= N + n/32 + 1): D is
+// built once in shared memory and held in registers by every warp (dreg),
+// every position runs all its stages there.
 template <int C>
 __global__ void __launch_bounds__(32 * kSparseWarps, 3) sparse_mulmod_regs_kernel(const SparseArgs args)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    uint32_t *D = smem + warp * (32u * C);
-    const uint32_t step = gridDim.x * kSparseWarps;
-    for (uint32_t p = blockIdx.x * kSparseWarps + warp; p < args.count; p += step) {
+    uint32_t *D = smem;                       // 32 C words
+    uint32_t *red = smem + 32u * C;           // 3 x 32 C words
+    uint32_t jb, je;
+    warp_share(args.w, warp, &jb, &je);
+    for (uint32_t p = blockIdx.x; p < args.count; p += gridDim.x) {
         const uint32_t *a32 = reinterpret_cast<const uint32_t *>(args.a + (size_t)p * args.stride_a);
         const uint32_t *pos = args.pos + (size_t)p * args.stride_pos;
-        build_doubled(D, 32u * C, a32, args.n, lane);
-        __syncwarp();
+        build_doubled(D, 32u * C, a32, args.n, threadIdx.x, blockDim.x);
+        __syncthreads();
         uint32_t dreg[C], acc[C];
 #pragma unroll
         for (int k = 0; k < C; ++k) {
             dreg[k] = D[lane * C + k];
             acc[k] = 0u;
         }
-        __syncwarp();
-        for (uint32_t j0 = 0; j0 < args.w; j0 += 32u) {
-            const uint32_t mine = j0 + lane < args.w ? pos[j0 + lane] : 0u;
-            const uint32_t cnt = args.w - j0 < 32u ? args.w - j0 : 32u;
+        for (uint32_t j0 = jb; j0 < je; j0 += 32u) {
+            const uint32_t mine = j0 + lane < je ? pos[j0 + lane] : 0u;
+            const uint32_t cnt = je - j0 < 32u ? je - j0 : 32u;
             for (uint32_t jj = 0; jj < cnt; ++jj) {
                 const uint32_t s = args.n - __shfl_sync(0xffffffffu, mine, jj);
                 uint32_t y[C];
@@ -133,35 +170,39 @@ __global__ void __launch_bounds__(32 * kSparseWarps, 3) sparse_mulmod_regs_kerne
                 add_window<C>(acc, y, s & 31u, lane);
             }
         }
-        store_result<C>(args.r + (size_t)p * args.stride_r, acc, args.n, lane);
+        reduce_and_store<C>(acc, red, 32u * C, args.r + (size_t)p * args.stride_r, args.n, lane, warp);
+        __syncthreads();   // D and red are rewritten for the next product
     }
 }
 
-// Larger n: D in shared memory; the `pre` largest shifts run there (the
-// first from D into B, the rest in place in B), then the register window
-// (32 C words of B, or of D when pre = 0) takes the remaining stages.
+// Larger n: D in shared memory, built once per product; each warp applies
+// the `pre` largest shifts of its positions in its own buffer B (the first
+// from D into B, the rest in place in B), then its register window (32 C
+// words of B, or of D when pre = 0) takes the remaining stages.  The B
+// buffers of warps 1-3 (b_words >= 32 C) hold the partial sums at the end.
 template <int C>
 __global__ void __launch_bounds__(32 * kSparseWarps) sparse_mulmod_staged_kernel(const SparseArgs args)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    uint32_t *D = smem + warp * (args.d_words + args.b_words);
-    uint32_t *B = D + args.d_words;
+    uint32_t *D = smem;
+    uint32_t *B = smem + args.d_words + warp * args.b_words;
     const uint32_t N = (args.n + 31u) / 32u;
-    const uint32_t step = gridDim.x * kSparseWarps;
-    for (uint32_t p = blockIdx.x * kSparseWarps + warp; p < args.count; p += step) {
+    uint32_t jb, je;
+    warp_share(args.w, warp, &jb, &je);
+    for (uint32_t p = blockIdx.x; p < args.count; p += gridDim.x) {
         const uint32_t *a32 = reinterpret_cast<const uint32_t *>(args.a + (size_t)p * args.stride_a);
         const uint32_t *pos = args.pos + (size_t)p * args.stride_pos;
-        build_doubled(D, args.d_words, a32, args.n, lane);
-        __syncwarp();
+        build_doubled(D, args.d_words, a32, args.n, threadIdx.x, blockDim.x);
+        __syncthreads();
         uint32_t acc[C];
 #pragma unroll
         for (int k = 0; k < C; ++k)
             acc[k] = 0u;
         const uint32_t *src = args.pre ? B : D;
-        for (uint32_t j0 = 0; j0 < args.w; j0 += 32u) {
-            const uint32_t mine = j0 + lane < args.w ? pos[j0 + lane] : 0u;
-            const uint32_t cnt = args.w - j0 < 32u ? args.w - j0 : 32u;
+        for (uint32_t j0 = jb; j0 < je; j0 += 32u) {
+            const uint32_t mine = j0 + lane < je ? pos[j0 + lane] : 0u;
+            const uint32_t cnt = je - j0 < 32u ? je - j0 : 32u;
             for (uint32_t jj = 0; jj < cnt; ++jj) {
                 const uint32_t s = args.n - __shfl_sync(0xffffffffu, mine, jj);
                 const uint32_t q = s >> 5;
@@ -200,7 +241,10 @@ __global__ void __launch_bounds__(32 * kSparseWarps) sparse_mulmod_staged_kernel
                 add_window<C>(acc, y, s & 31u, lane);
             }
         }
-        store_result<C>(args.r + (size_t)p * args.stride_r, acc, args.n, lane);
+        __syncthreads();   // every warp is done with D and with its B
+        reduce_and_store<C>(acc, smem + args.d_words + args.b_words, args.b_words,
+                            args.r + (size_t)p * args.stride_r, args.n, lane, warp);
+        __syncthreads();   // D and the B buffers are rewritten for the next product
     }
 }
 
@@ -215,7 +259,7 @@ static cudaError_t launch_regs(const SparseArgs &a, unsigned grid, cudaStream_t 
 template <int C>
 static cudaError_t launch_staged(const SparseArgs &a, unsigned grid, cudaStream_t st)
 {
-    const size_t smem = 4ull * kSparseWarps * (a.d_words + a.b_words);
+    const size_t smem = 4ull * (a.d_words + kSparseWarps * a.b_words);
     cudaError_t e = cudaFuncSetAttribute(sparse_mulmod_staged_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess)
@@ -260,7 +304,8 @@ bool sparse_shape(uint32_t n, SparseShape *sh)
             sh->staged = 1;
             sh->pre = pre;
             sh->d_words = pre == 0 ? M : (N + (1u << T) > M ? N + (1u << T) : M);
-            sh->b_words = pre == 0 ? 0u : (N + (1u << (T - 1u)) > M ? N + (1u << (T - 1u)) : M);
+            // B: the shared stages' buffer, and the partial sums at the end
+            sh->b_words = pre == 0 ? M : (N + (1u << (T - 1u)) > M ? N + (1u << (T - 1u)) : M);
             return true;
         }
     }
@@ -269,12 +314,12 @@ bool sparse_shape(uint32_t n, SparseShape *sh)
 
 size_t sparse_smem_bytes(const SparseShape &sh)
 {
-    return sh.staged ? 4ull * kSparseWarps * (sh.d_words + sh.b_words) : 4ull * kSparseWarps * 32u * sh.C;
+    return sh.staged ? 4ull * (sh.d_words + kSparseWarps * sh.b_words) : 4ull * kSparseWarps * 32u * sh.C;
 }
 
 cudaError_t launch_sparse_mulmod(const SparseArgs &args, const SparseShape &sh, int sm_count, cudaStream_t st)
 {
-    const size_t ctas = (args.count + kSparseWarps - 1) / kSparseWarps;
+    const size_t ctas = args.count;   // one CTA per product
     const size_t cap = (size_t)(sm_count > 0 ? sm_count : 1) * 8u;
     const unsigned grid = (unsigned)(ctas < cap ? ctas : cap);
     if (grid == 0)
