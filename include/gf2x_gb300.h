@@ -303,6 +303,23 @@ gf2x_status gf2x_mulmod_sparse(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a, co
                                uint32_t n, size_t count, size_t stride_a, size_t stride_pos, size_t stride_r,
                                gf2x_stream stream);
 
+/* The kernel shape gf2x_mulmod_sparse uses for n (host only, needs no GPU).
+ * The warp's cyclic window is 32 x words_per_lane words; the word offset's
+ * bits are applied by shared_stages shifts in shared memory (the largest,
+ * each >= 256 words) and then register_stages shifts in registers
+ * (shared_stages + register_stages = bits of n/32).  GF2X_EUNSUPPORTED for n
+ * outside [1, 65536]. */
+typedef struct {
+    uint32_t n;
+    uint32_t words_per_lane;
+    uint32_t shared_stages;
+    uint32_t register_stages;
+    uint32_t doubled_in_registers;  /* 1: a + X^n a itself stays in registers */
+    uint32_t smem_bytes;            /* dynamic shared memory per CTA (four warps) */
+} gf2x_sparse_info;
+
+gf2x_status gf2x_sparse_info_get(uint32_t n, gf2x_sparse_info *info);
+
 /* Build and upload (synchronously on `stream`) the current plans of the
  * given sizes, so that later calls and CUDA graph captures find them ready,
  * and make exactly these sizes the ones device-item batches accept (their

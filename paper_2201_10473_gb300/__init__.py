@@ -12,7 +12,7 @@ sm_103a behind the C ABI of include/gf2x_gb300.h:
   serve.py     continuous-batching request loop
 """
 from .gf2x import (Context, Gf2xError, default_spec, full_limbs, lib, limbs, pack_items, parse_spec,  # noqa: F401
-                   plan_info, spec_text)
+                   plan_info, sparse_info, spec_text)
 
-__all__ = ["Context", "Gf2xError", "default_spec", "plan_info", "limbs", "full_limbs", "lib", "parse_spec",
+__all__ = ["Context", "Gf2xError", "default_spec", "plan_info", "sparse_info", "limbs", "full_limbs", "lib", "parse_spec",
            "spec_text", "pack_items"]

@@ -861,6 +861,22 @@ extern "C" gf2x_status gf2x_mulmod_sparse(gf2x_ctx *ctx, uint64_t *r, const uint
     return GF2X_OK;
 }
 
+extern "C" gf2x_status gf2x_sparse_info_get(uint32_t n, gf2x_sparse_info *info)
+{
+    if (!info)
+        return GF2X_EINVAL;
+    SparseShape sh;
+    if (!sparse_shape(n, &sh))
+        return GF2X_EUNSUPPORTED;
+    info->n = n;
+    info->words_per_lane = sh.C;
+    info->shared_stages = sh.pre;
+    info->register_stages = sh.T - sh.pre;
+    info->doubled_in_registers = sh.staged ? 0u : 1u;
+    info->smem_bytes = (uint32_t)sparse_smem_bytes(sh);
+    return GF2X_OK;
+}
+
 // k rows of `width` limbs, `dpitch` / `spitch` limbs apart.
 static cudaError_t copy_rows(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, size_t k,
                              cudaMemcpyKind kind, cudaStream_t st)

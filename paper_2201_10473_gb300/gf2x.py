@@ -82,6 +82,7 @@ _SIGNATURES = {
     "gf2x_mul_strided_host": ([_P, _P, _P, _P, _U32, _SZ, _SZ, _SZ, _U32, _P], _I),
     "gf2x_mul_unbalanced": ([_P, _P, _P, _U32, _SZ, _P, _U32, _SZ, _SZ, _SZ, _P], _I),
     "gf2x_mulmod_sparse": ([_P, _P, _P, _P, _U32, _U32, _SZ, _SZ, _SZ, _SZ, _P], _I),
+    "gf2x_sparse_info_get": ([_U32, _P], _I),
     "gf2x_mul_batched": ([_P, _P, _SZ, _U32, _P], _I),
     "gf2x_ctx_prepare": ([_P, ctypes.POINTER(_U32), _SZ, _P], _I),
     "gf2x_ctx_launch_shape": ([_P, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32),
@@ -155,6 +156,20 @@ def plan_info(n: int, spec: str | None = None) -> dict:
     d["level_words"] = [info.level_words[i] for i in range(s.nlev + 1)]
     d["spec"] = spec_text(s)
     return d
+
+
+class SparseInfo(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint32) for f in ("n", "words_per_lane", "shared_stages", "register_stages",
+                                               "doubled_in_registers", "smem_bytes")]
+
+
+def sparse_info(n: int) -> dict:
+    """Kernel shape of the constant-time sparse product for size n; host only."""
+    info = SparseInfo()
+    st = lib().gf2x_sparse_info_get(n, ctypes.byref(info))
+    if st:
+        raise Gf2xError(st, "gf2x_sparse_info_get", f"n={n}")
+    return {f: getattr(info, f) for f, _ in SparseInfo._fields_}
 
 
 # ------------------------------------------------------------------ context
