@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="hqc128")
     p.add_argument("--no-plain", action="store_true", help="skip the plain one-launch-per-product measurement")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle cpu_baseline sample")
-    p.add_argument("--no-extras", action="store_true", help="skip the other workloads (C1, C3, C4, shared key, unbalanced, sparse, C5)")
+    p.add_argument("--no-extras", action="store_true", help="skip the other workloads (C1, C3, C4, shared key, unbalanced, sparse, Toom-4, C5)")
     p.add_argument("--serving-requests", type=int, default=200000)
     p.add_argument("--plan", default=None, help="plan spec for the main workload (default: the tuned database)")
     return p.parse_args()
@@ -805,6 +805,37 @@ def run_sparse(device):
     return res
 
 
+def run_toom4(device):
+    """Toom-4 top level against the regular path (the tuned or default plan)
+    at 57637, 100000 and 131072 bits, 512 products mod X^n - 1 each."""
+    import torch
+
+    import oracle
+    from paper_2201_10473_gb300 import Context
+    res = {"workload": "toom4-top-level-mulmod"}
+    for n in (57637, 100000, 131072):
+        count = 512
+        ctx = Context(device, batch_hint=count)
+        a, b = wl.dense_pair(wl.BASE_SEED + 11, n, count)
+        da, db = _dev(a), _dev(b)
+        out = torch.empty((count, wl.limbs(n)), dtype=torch.int64, device="cuda")
+        rates = {}
+        for rep in range(2):
+            for name, fn in (("toom4", lambda: ctx.mul_toom4(da, db, n, True, out=out)),
+                             ("regular", lambda: ctx.mul_strided(da, db, n, True, out=out, persistent=True))):
+                ms = _time_calls(fn, 5, 2)
+                rates.setdefault(name, []).append(count / (ms * 1e-3))
+        ctx.mul_toom4(da, db, n, True, out=out)
+        got = _host(out)
+        ok = all(np.array_equal(got[p], oracle.mulmod(a[p], b[p], n)) for p in (0, count - 1))
+        plan = ctx.get_plan(n)
+        ctx.close()
+        t4, rg = max(rates["toom4"]), max(rates["regular"])
+        res[f"n{n}"] = {"products": count, "toom4_mults_per_s": t4, "regular_mults_per_s": rg,
+                        "toom4_over_regular": t4 / rg, "regular_plan": plan, "sample_checked_against_oracle": ok}
+    return res
+
+
 def run_c5(device, requests):
     """Serving: Poisson arrivals, HBM-budget admission, continuous batching."""
     import torch  # noqa: F401
@@ -889,7 +920,7 @@ def run_extras(args, device):
     res = {}
     for name, fn in (("c1", lambda: run_c1(device)), ("c3", lambda: run_c3(device)), ("c4", lambda: run_c4(device)),
                      ("shared_key", lambda: run_shared(device)), ("unbalanced", lambda: run_unbalanced(device)),
-                     ("sparse_ct", lambda: run_sparse(device)),
+                     ("sparse_ct", lambda: run_sparse(device)), ("toom4", lambda: run_toom4(device)),
                      ("c5", lambda: run_c5(device, args.serving_requests))):
         t0 = time.time()
         try:

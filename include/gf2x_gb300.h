@@ -303,6 +303,22 @@ gf2x_status gf2x_mulmod_sparse(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a, co
                                uint32_t n, size_t count, size_t stride_a, size_t stride_pos, size_t stride_r,
                                gf2x_stream stream);
 
+/* `count` products of one size n through a Toom-4 top level (Toom-Cook
+ * 4-7, the next member of Sec. 3's Toom-Cook family after Toom-3; in the
+ * size ranges of gf2x quoted in Table tab:compToom it takes over from
+ * Toom-3 above degree 22143, with a "gray zone" where the two are close).  Same
+ * operands, strides, flags (GF2X_REDUCE) and results as gf2x_mul_strided.
+ * Each operand is cut into four parts of m = ceil(ceil(n/32)/4) 32-bit
+ * words and evaluated at 0, 1, x, x+1, x^2, x^2+1 and inf with x = X^32
+ * (an evaluation kernel); the seven products of E = m + 6 (rounded up to
+ * even) words run as one batch under the context's plan for 32 E bits;
+ * an interpolation kernel (exact divisions by x, x+1 and x^2+x+1 as word
+ * shifts and prefix XORs) recomposes, and folds mod X^n - 1 on request.
+ * Scratch: the context buffer of gf2x_mul_unbalanced (112 E bytes per
+ * product, groups of at most 256 MiB).  Errors: as gf2x_mul_strided. */
+gf2x_status gf2x_mul_toom4(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n,
+                           size_t count, size_t stride_in, size_t stride_out, uint32_t flags, gf2x_stream stream);
+
 /* The kernel shape gf2x_mulmod_sparse uses for n (host only, needs no GPU).
  * The warp's cyclic window is 32 x words_per_lane words; the word offset's
  * bits are applied by shared_stages shifts in shared memory (the largest,

@@ -667,6 +667,52 @@ static gf2x_status strided_on_slot(gf2x_ctx *ctx, uint32_t slot, uint64_t *out, 
                   (batch_flags & GF2X_BATCH_PERSISTENT) != 0, s);
 }
 
+// The context scratch of the unbalanced and Toom-4 calls: at least `want`
+// bytes (grows only; cudaFree synchronizes the device, so no call still
+// uses the old buffer), ordered after the previous call that used it when
+// that came on another stream.  scratch_release records the ordering event.
+static gf2x_status scratch_acquire(gf2x_ctx *ctx, size_t want, cudaStream_t s)
+{
+    if (ctx->ub_bytes < want) {
+        if (ctx->ub) {
+            cudaError_t e = cudaFree(ctx->ub);
+            ctx->ub = nullptr;
+            ctx->ub_bytes = 0;
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e, "scratch");
+        }
+        cudaError_t e = cudaMalloc((void **)&ctx->ub, want);
+        if (e != cudaSuccess) {
+            ctx->ub = nullptr;
+            return e == cudaErrorMemoryAllocation ? fail(ctx, GF2X_ENOMEM, "scratch") : cuda_fail(ctx, e, "scratch");
+        }
+        ctx->ub_bytes = want;
+    }
+    if (!ctx->ub_done) {
+        cudaError_t e = cudaEventCreateWithFlags(&ctx->ub_done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            ctx->ub_done = nullptr;
+            return cuda_fail(ctx, e, "scratch event");
+        }
+    }
+    if (ctx->ub_used && ctx->ub_stream != s) {
+        cudaError_t e = cudaStreamWaitEvent(s, ctx->ub_done, 0);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "scratch ordering");
+    }
+    return GF2X_OK;
+}
+
+static gf2x_status scratch_release(gf2x_ctx *ctx, cudaStream_t s)
+{
+    cudaError_t e = cudaEventRecord(ctx->ub_done, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "scratch event");
+    ctx->ub_used = true;
+    ctx->ub_stream = s;
+    return GF2X_OK;
+}
+
 // The plan slot and modelled operations of a product of size n in an
 // unbalanced call: the context's current plan for n; for the chunk size m
 // (= 64 ceil(nb/64)) without a plan of its own, the spec of nb's plan where
@@ -757,37 +803,9 @@ extern "C" gf2x_status gf2x_mul_unbalanced(gf2x_ctx *ctx, uint64_t *out, const u
     // scratch per product: chunks x (two operand rows + one product row)
     const size_t per = 8ull * chunks * (2ull * Ld + Wp);
     const size_t group = std::max<size_t>(1, std::min<size_t>(count, kWorkspaceCap / per));
-    const size_t want = group * per;
-    if (ctx->ub_bytes < want) {
-        if (ctx->ub) {
-            cudaError_t e = cudaFree(ctx->ub);   // synchronizes the device: no call still uses it
-            ctx->ub = nullptr;
-            ctx->ub_bytes = 0;
-            if (e != cudaSuccess)
-                return cuda_fail(ctx, e, "unbalanced scratch");
-        }
-        cudaError_t e = cudaMalloc((void **)&ctx->ub, want);
-        if (e != cudaSuccess) {
-            ctx->ub = nullptr;
-            return e == cudaErrorMemoryAllocation ? fail(ctx, GF2X_ENOMEM, "unbalanced scratch")
-                                                  : cuda_fail(ctx, e, "unbalanced scratch");
-        }
-        ctx->ub_bytes = want;
-    }
-    if (!ctx->ub_done) {
-        cudaError_t e = cudaEventCreateWithFlags(&ctx->ub_done, cudaEventDisableTiming);
-        if (e != cudaSuccess) {
-            ctx->ub_done = nullptr;
-            return cuda_fail(ctx, e, "unbalanced scratch event");
-        }
-    }
-    // the scratch is shared by every call of the context: order this call
-    // after the previous one when that came on another stream
-    if (ctx->ub_used && ctx->ub_stream != s) {
-        cudaError_t e = cudaStreamWaitEvent(s, ctx->ub_done, 0);
-        if (e != cudaSuccess)
-            return cuda_fail(ctx, e, "unbalanced scratch ordering");
-    }
+    gf2x_status sst = scratch_acquire(ctx, group * per, s);
+    if (sst != GF2X_OK)
+        return sst;
     for (size_t c0 = 0; c0 < count; c0 += group) {
         const size_t g = std::min(group, count - c0);
         uint64_t *A = ctx->ub, *B = A + g * chunks * Ld, *P = B + g * chunks * Ld;
@@ -806,12 +824,7 @@ extern "C" gf2x_status gf2x_mul_unbalanced(gf2x_ctx *ctx, uint64_t *out, const u
         if (e != cudaSuccess)
             return cuda_fail(ctx, e, "overlap-add launch");
     }
-    cudaError_t e = cudaEventRecord(ctx->ub_done, s);
-    if (e != cudaSuccess)
-        return cuda_fail(ctx, e, "unbalanced scratch event");
-    ctx->ub_used = true;
-    ctx->ub_stream = s;
-    return GF2X_OK;
+    return scratch_release(ctx, s);
 }
 
 extern "C" gf2x_status gf2x_mulmod_sparse(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a, const uint32_t *pos,
@@ -875,6 +888,64 @@ extern "C" gf2x_status gf2x_sparse_info_get(uint32_t n, gf2x_sparse_info *info)
     info->doubled_in_registers = sh.staged ? 0u : 1u;
     info->smem_bytes = (uint32_t)sparse_smem_bytes(sh);
     return GF2X_OK;
+}
+
+extern "C" gf2x_status gf2x_mul_toom4(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n,
+                                      size_t count, size_t stride_in, size_t stride_out, uint32_t flags,
+                                      gf2x_stream stream)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    if (count == 0)
+        return GF2X_OK;
+    if (n < 1 || n > GF2X_MAX_N)
+        return fail(ctx, GF2X_EUNSUPPORTED, "n outside [1, 131072]");
+    gf2x_status st = check_operands(ctx, out, a, b, n, flags, count, stride_in, stride_out);
+    if (st != GF2X_OK)
+        return st;
+    Toom4Args t;
+    memset(&t, 0, sizeof(t));
+    if (!toom4_shape(n, &t))
+        return fail(ctx, GF2X_EUNSUPPORTED, "no Toom-4 shape for this n");
+    cudaStream_t s = (cudaStream_t)stream;
+    // the seven children: full products of 32 E bits, E/2 limbs per operand
+    uint32_t slot;
+    st = plan_for(ctx, 32u * t.E, s, &slot);
+    if (st != GF2X_OK)
+        return st;
+    const size_t per = 4ull * 28u * t.E;   // 7 operand slots and 7 products of 2E words
+    const size_t group = std::max<size_t>(1, std::min<size_t>(count, kWorkspaceCap / per));
+    st = scratch_acquire(ctx, group * per, s);
+    if (st != GF2X_OK)
+        return st;
+    t.stride_in = stride_in;
+    t.stride_out = stride_out;
+    t.n = n;
+    t.flags = flags;
+    for (size_t c0 = 0; c0 < count; c0 += group) {
+        const size_t g = std::min(group, count - c0);
+        uint32_t *opnd = reinterpret_cast<uint32_t *>(ctx->ub);
+        uint32_t *prod = opnd + g * 14u * t.E;
+        t.a = a + c0 * stride_in;
+        t.b = b + c0 * stride_in;
+        t.out = out + c0 * stride_out;
+        t.count = (uint32_t)g;
+        t.opnd = opnd;
+        t.prod = prod;
+        const unsigned grid = (unsigned)std::min<size_t>(g, 8ull * ctx->sm_count);
+        cudaError_t e = launch_toom4_eval(t, grid, s);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "Toom-4 evaluation launch");
+        const uint64_t *ca = reinterpret_cast<const uint64_t *>(opnd);
+        st = strided_on_slot(ctx, slot, reinterpret_cast<uint64_t *>(prod), ca, ca + t.E / 2u, 7u * g, t.E, t.E, 0u,
+                             GF2X_BATCH_PERSISTENT, s);
+        if (st != GF2X_OK)
+            return st;
+        e = launch_toom4_interp(t, grid, s);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "Toom-4 interpolation launch");
+    }
+    return scratch_release(ctx, s);
 }
 
 // k rows of `width` limbs, `dpitch` / `spitch` limbs apart.

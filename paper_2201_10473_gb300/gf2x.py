@@ -83,6 +83,7 @@ _SIGNATURES = {
     "gf2x_mul_unbalanced": ([_P, _P, _P, _U32, _SZ, _P, _U32, _SZ, _SZ, _SZ, _P], _I),
     "gf2x_mulmod_sparse": ([_P, _P, _P, _P, _U32, _U32, _SZ, _SZ, _SZ, _SZ, _P], _I),
     "gf2x_sparse_info_get": ([_U32, _P], _I),
+    "gf2x_mul_toom4": ([_P, _P, _P, _P, _U32, _SZ, _SZ, _SZ, _U32, _P], _I),
     "gf2x_mul_batched": ([_P, _P, _SZ, _U32, _P], _I),
     "gf2x_ctx_prepare": ([_P, ctypes.POINTER(_U32), _SZ, _P], _I),
     "gf2x_ctx_launch_shape": ([_P, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32),
@@ -321,6 +322,24 @@ class Context:
         self._raise(lib().gf2x_mul_unbalanced(self._h, O.data_ptr(), A.data_ptr(), na, A.shape[1], B.data_ptr(), nb,
                                               B.shape[1], count, O.shape[1], _stream_handle(stream)),
                     "gf2x_mul_unbalanced")
+        return out
+
+    def mul_toom4(self, a: torch.Tensor, b: torch.Tensor, n: int, reduce: bool, out: torch.Tensor | None = None,
+                  stream=None):
+        """mul_strided through a Toom-4 top level (seven child products per row)."""
+        if a.dim() != 2 or a.shape != b.shape:
+            raise ValueError("a and b must be equal-shaped 2-D tensors")
+        _check_operand(a, n, "a")
+        _check_operand(b, n, "b")
+        count = a.shape[0]
+        ol = limbs(n) if reduce else full_limbs(n)
+        if out is None:
+            out = torch.empty((count, ol), dtype=torch.int64, device=a.device)
+        if out.dim() != 2 or out.shape[0] != count or out.shape[1] < ol or not out.is_contiguous():
+            raise ValueError("bad output tensor")
+        self._raise(lib().gf2x_mul_toom4(self._h, out.data_ptr(), a.data_ptr(), b.data_ptr(), n, count, a.shape[1],
+                                         out.shape[1], REDUCE if reduce else 0, _stream_handle(stream)),
+                    "gf2x_mul_toom4")
         return out
 
     def mulmod_sparse(self, a: torch.Tensor, pos: torch.Tensor, n: int, out: torch.Tensor | None = None,

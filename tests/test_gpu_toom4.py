@@ -1,0 +1,74 @@
+"""Toom-4 top level (gf2x_mul_toom4): every row equals the product of the
+regular path (gf2x_mul_strided) bit for bit, and the oracle's on samples,
+full and reduced, from one-word operands up to n = 131072, with garbage
+above n, padded strides, and batches larger than one scratch group."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as wl
+from gpu_util import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n,count", [
+    (1, 3), (33, 3), (129, 5), (257, 4), (4096, 9), (17669, 37), (57637, 5), (100000, 3), (131072, 3),
+])
+@pytest.mark.parametrize("reduce", [False, True])
+def test_matches_regular_path_and_oracle(n, count, reduce):
+    from paper_2201_10473_gb300 import Context
+    ctx = Context(0)
+    try:
+        a, b = wl.dense_pair(9990 + n, n, count)
+        a_g = a.copy()
+        if n % 64:                                     # bits above n must be ignored
+            a_g[:, -1] |= ~np.uint64((1 << (n % 64)) - 1)
+        got = ctx.mul_toom4(to_dev(a_g), to_dev(b), n, reduce)
+        ref = ctx.mul_strided(to_dev(a), to_dev(b), n, reduce, persistent=True)
+        ctx.sync_status()
+        assert torch.equal(got, ref)
+        host = to_host(got)
+        for p in sorted({0, count - 1}):
+            exp = oracle.mulmod(a[p], b[p], n) if reduce else oracle.mul(a[p], b[p], n)
+            assert np.array_equal(host[p][: len(exp)], exp), p
+    finally:
+        ctx.close()
+
+
+def test_padded_strides():
+    from paper_2201_10473_gb300 import Context, gf2x
+    n, count = 24659, 6
+    L = wl.limbs(n)
+    ctx = Context(0)
+    try:
+        a, b = wl.dense_pair(9991, n, count)
+        pad = np.full((count, 3), np.uint64(0x3C3C3C3C3C3C3C3C))
+        da, db = to_dev(np.concatenate([a, pad], 1)), to_dev(np.concatenate([b, pad], 1))
+        out = torch.full((count, L + 2), -1, dtype=torch.int64, device="cuda")
+        st = gf2x.lib().gf2x_mul_toom4(ctx._h, out.data_ptr(), da.data_ptr(), db.data_ptr(), n, count, L + 3, L + 2,
+                                       gf2x.REDUCE, None)
+        assert st == 0
+        torch.cuda.synchronize()
+        host = to_host(out)
+        for p in range(count):
+            assert np.array_equal(host[p, :L], oracle.mulmod(a[p], b[p], n)), p
+        assert (host[:, L:] == np.uint64(0xFFFFFFFFFFFFFFFF)).all()
+    finally:
+        ctx.close()
+
+
+def test_batch_larger_than_one_scratch_group():
+    """At n = 131072 a product needs 115 KiB of scratch: 2400 products run as
+    two groups of the 256 MiB buffer."""
+    from paper_2201_10473_gb300 import Context
+    n, count = 131072, 2400
+    ctx = Context(0)
+    try:
+        a, b = wl.dense_pair(9992, n, count)
+        got = to_host(ctx.mul_toom4(to_dev(a), to_dev(b), n, True))
+        for p in (0, 2327, 2328, count - 1):
+            assert np.array_equal(got[p], oracle.mulmod(a[p], b[p], n)), p
+    finally:
+        ctx.close()
