@@ -806,13 +806,14 @@ def run_sparse(device):
 
 
 def run_toom4(device):
-    """Toom-4 top level against the regular path (the tuned or default plan)
-    at 57637, 100000 and 131072 bits, 512 products mod X^n - 1 each."""
+    """Toom-4 and Toom-5 top levels against the regular path (the tuned or
+    default plan) at 57637, 100000 and 131072 bits, 512 products mod X^n - 1
+    each."""
     import torch
 
     import oracle
     from paper_2201_10473_gb300 import Context
-    res = {"workload": "toom4-top-level-mulmod"}
+    res = {"workload": "toom4-toom5-top-level-mulmod"}
     for n in (57637, 100000, 131072):
         count = 512
         ctx = Context(device, batch_hint=count)
@@ -822,17 +823,21 @@ def run_toom4(device):
         rates = {}
         for rep in range(2):
             for name, fn in (("toom4", lambda: ctx.mul_toom4(da, db, n, True, out=out)),
+                             ("toom5", lambda: ctx.mul_toom5(da, db, n, True, out=out)),
                              ("regular", lambda: ctx.mul_strided(da, db, n, True, out=out, persistent=True))):
                 ms = _time_calls(fn, 5, 2)
                 rates.setdefault(name, []).append(count / (ms * 1e-3))
-        ctx.mul_toom4(da, db, n, True, out=out)
-        got = _host(out)
-        ok = all(np.array_equal(got[p], oracle.mulmod(a[p], b[p], n)) for p in (0, count - 1))
+        ok = True
+        for fn in (ctx.mul_toom4, ctx.mul_toom5):
+            fn(da, db, n, True, out=out)
+            got = _host(out)
+            ok &= all(np.array_equal(got[p], oracle.mulmod(a[p], b[p], n)) for p in (0, count - 1))
         plan = ctx.get_plan(n)
         ctx.close()
-        t4, rg = max(rates["toom4"]), max(rates["regular"])
-        res[f"n{n}"] = {"products": count, "toom4_mults_per_s": t4, "regular_mults_per_s": rg,
-                        "toom4_over_regular": t4 / rg, "regular_plan": plan, "sample_checked_against_oracle": ok}
+        t4, t5, rg = max(rates["toom4"]), max(rates["toom5"]), max(rates["regular"])
+        res[f"n{n}"] = {"products": count, "toom4_mults_per_s": t4, "toom5_mults_per_s": t5,
+                        "regular_mults_per_s": rg, "toom4_over_regular": t4 / rg, "toom5_over_regular": t5 / rg,
+                        "regular_plan": plan, "sample_checked_against_oracle": ok}
     return res
 
 

@@ -319,6 +319,14 @@ gf2x_status gf2x_mulmod_sparse(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a, co
 gf2x_status gf2x_mul_toom4(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n,
                            size_t count, size_t stride_in, size_t stride_out, uint32_t flags, gf2x_stream stream);
 
+/* The same through a Toom-5 top level (Toom-Cook 5-9, the next range of
+ * Table tab:compToom): five parts of m = ceil(ceil(n/32)/5) words, nine
+ * points (those of gf2x_mul_toom4 plus x^2+x and x^2+x+1, whose
+ * differences again factor into x, x+1 and x^2+x+1), nine child products of
+ * E = m + 8 (even) words; scratch 144 E bytes per product. */
+gf2x_status gf2x_mul_toom5(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n,
+                           size_t count, size_t stride_in, size_t stride_out, uint32_t flags, gf2x_stream stream);
+
 /* The kernel shape gf2x_mulmod_sparse uses for n (host only, needs no GPU).
  * The warp's cyclic window is 32 x words_per_lane words; the word offset's
  * bits are applied by shared_stages shifts in shared memory (the largest,

@@ -890,9 +890,11 @@ extern "C" gf2x_status gf2x_sparse_info_get(uint32_t n, gf2x_sparse_info *info)
     return GF2X_OK;
 }
 
-extern "C" gf2x_status gf2x_mul_toom4(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n,
-                                      size_t count, size_t stride_in, size_t stride_out, uint32_t flags,
-                                      gf2x_stream stream)
+// A Toom-K top level (K = 4 or 5): evaluation kernel, the 2K - 1 child
+// products of every row as one strided batch, interpolation kernel.
+static gf2x_status run_toom(gf2x_ctx *ctx, uint32_t K, uint64_t *out, const uint64_t *a, const uint64_t *b,
+                            uint32_t n, size_t count, size_t stride_in, size_t stride_out, uint32_t flags,
+                            gf2x_stream stream)
 {
     if (!ctx)
         return GF2X_EINVAL;
@@ -903,17 +905,18 @@ extern "C" gf2x_status gf2x_mul_toom4(gf2x_ctx *ctx, uint64_t *out, const uint64
     gf2x_status st = check_operands(ctx, out, a, b, n, flags, count, stride_in, stride_out);
     if (st != GF2X_OK)
         return st;
-    Toom4Args t;
+    ToomArgs t;
     memset(&t, 0, sizeof(t));
-    if (!toom4_shape(n, &t))
-        return fail(ctx, GF2X_EUNSUPPORTED, "no Toom-4 shape for this n");
+    if (!toom_shape(K, n, &t))
+        return fail(ctx, GF2X_EUNSUPPORTED, "no Toom shape for this n");
     cudaStream_t s = (cudaStream_t)stream;
-    // the seven children: full products of 32 E bits, E/2 limbs per operand
+    const uint32_t NP = 2u * K - 1u;
+    // the children: full products of 32 E bits, E/2 limbs per operand
     uint32_t slot;
     st = plan_for(ctx, 32u * t.E, s, &slot);
     if (st != GF2X_OK)
         return st;
-    const size_t per = 4ull * 28u * t.E;   // 7 operand slots and 7 products of 2E words
+    const size_t per = 4ull * 4u * NP * t.E;   // NP operand slots and NP products of 2E words
     const size_t group = std::max<size_t>(1, std::min<size_t>(count, kWorkspaceCap / per));
     st = scratch_acquire(ctx, group * per, s);
     if (st != GF2X_OK)
@@ -925,7 +928,7 @@ extern "C" gf2x_status gf2x_mul_toom4(gf2x_ctx *ctx, uint64_t *out, const uint64
     for (size_t c0 = 0; c0 < count; c0 += group) {
         const size_t g = std::min(group, count - c0);
         uint32_t *opnd = reinterpret_cast<uint32_t *>(ctx->ub);
-        uint32_t *prod = opnd + g * 14u * t.E;
+        uint32_t *prod = opnd + g * 2u * NP * t.E;
         t.a = a + c0 * stride_in;
         t.b = b + c0 * stride_in;
         t.out = out + c0 * stride_out;
@@ -933,19 +936,33 @@ extern "C" gf2x_status gf2x_mul_toom4(gf2x_ctx *ctx, uint64_t *out, const uint64
         t.opnd = opnd;
         t.prod = prod;
         const unsigned grid = (unsigned)std::min<size_t>(g, 8ull * ctx->sm_count);
-        cudaError_t e = launch_toom4_eval(t, grid, s);
+        cudaError_t e = launch_toom_eval(K, t, grid, s);
         if (e != cudaSuccess)
-            return cuda_fail(ctx, e, "Toom-4 evaluation launch");
+            return cuda_fail(ctx, e, "Toom evaluation launch");
         const uint64_t *ca = reinterpret_cast<const uint64_t *>(opnd);
-        st = strided_on_slot(ctx, slot, reinterpret_cast<uint64_t *>(prod), ca, ca + t.E / 2u, 7u * g, t.E, t.E, 0u,
+        st = strided_on_slot(ctx, slot, reinterpret_cast<uint64_t *>(prod), ca, ca + t.E / 2u, NP * g, t.E, t.E, 0u,
                              GF2X_BATCH_PERSISTENT, s);
         if (st != GF2X_OK)
             return st;
-        e = launch_toom4_interp(t, grid, s);
+        e = launch_toom_interp(K, t, grid, s);
         if (e != cudaSuccess)
-            return cuda_fail(ctx, e, "Toom-4 interpolation launch");
+            return cuda_fail(ctx, e, "Toom interpolation launch");
     }
     return scratch_release(ctx, s);
+}
+
+extern "C" gf2x_status gf2x_mul_toom4(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n,
+                                      size_t count, size_t stride_in, size_t stride_out, uint32_t flags,
+                                      gf2x_stream stream)
+{
+    return run_toom(ctx, 4u, out, a, b, n, count, stride_in, stride_out, flags, stream);
+}
+
+extern "C" gf2x_status gf2x_mul_toom5(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n,
+                                      size_t count, size_t stride_in, size_t stride_out, uint32_t flags,
+                                      gf2x_stream stream)
+{
+    return run_toom(ctx, 5u, out, a, b, n, count, stride_in, stride_out, flags, stream);
 }
 
 // k rows of `width` limbs, `dpitch` / `spitch` limbs apart.

@@ -49,20 +49,20 @@ bool sparse_shape(uint32_t n, SparseShape *sh);
 size_t sparse_smem_bytes(const SparseShape &sh);
 cudaError_t launch_sparse_mulmod(const SparseArgs &args, const SparseShape &sh, int sm_count, cudaStream_t st);
 
-// Toom-4 top level (toom4.cu)
-struct Toom4Args {
+// Toom-4 and Toom-5 top levels (toom.cu)
+struct ToomArgs {
     const uint64_t *a, *b;    // operand rows, stride_in limbs apart
     uint64_t *out;            // result rows, stride_out limbs apart
     size_t stride_in, stride_out;
     uint32_t n, count, flags;
     uint32_t m, E, W, OW;     // part words, child operand words, interpolation and product buffer words
-    uint32_t *opnd;           // per product 7 slots of 2E words (A(p_j) | B(p_j))
-    const uint32_t *prod;     // per product 7 child products of 2E words
+    uint32_t *opnd;           // per product 2K - 1 slots of 2E words (A(p_j) | B(p_j))
+    const uint32_t *prod;     // per product 2K - 1 child products of 2E words
 };
-bool toom4_shape(uint32_t n, Toom4Args *a);
-size_t toom4_interp_smem(const Toom4Args &a);
-cudaError_t launch_toom4_eval(const Toom4Args &a, unsigned grid, cudaStream_t st);
-cudaError_t launch_toom4_interp(const Toom4Args &a, unsigned grid, cudaStream_t st);
+bool toom_shape(uint32_t K, uint32_t n, ToomArgs *a);
+size_t toom_interp_smem(uint32_t K, const ToomArgs &a);
+cudaError_t launch_toom_eval(uint32_t K, const ToomArgs &a, unsigned grid, cudaStream_t st);
+cudaError_t launch_toom_interp(uint32_t K, const ToomArgs &a, unsigned grid, cudaStream_t st);
 
 typedef cudaError_t (*LaunchFn)(const LaunchArgs &, unsigned, unsigned, size_t, cudaStream_t);
 typedef cudaError_t (*PrepareFn)(int *, unsigned, size_t);

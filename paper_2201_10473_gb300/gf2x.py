@@ -84,6 +84,7 @@ _SIGNATURES = {
     "gf2x_mulmod_sparse": ([_P, _P, _P, _P, _U32, _U32, _SZ, _SZ, _SZ, _SZ, _P], _I),
     "gf2x_sparse_info_get": ([_U32, _P], _I),
     "gf2x_mul_toom4": ([_P, _P, _P, _P, _U32, _SZ, _SZ, _SZ, _U32, _P], _I),
+    "gf2x_mul_toom5": ([_P, _P, _P, _P, _U32, _SZ, _SZ, _SZ, _U32, _P], _I),
     "gf2x_mul_batched": ([_P, _P, _SZ, _U32, _P], _I),
     "gf2x_ctx_prepare": ([_P, ctypes.POINTER(_U32), _SZ, _P], _I),
     "gf2x_ctx_launch_shape": ([_P, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32),
@@ -327,6 +328,14 @@ class Context:
     def mul_toom4(self, a: torch.Tensor, b: torch.Tensor, n: int, reduce: bool, out: torch.Tensor | None = None,
                   stream=None):
         """mul_strided through a Toom-4 top level (seven child products per row)."""
+        return self._toom("gf2x_mul_toom4", a, b, n, reduce, out, stream)
+
+    def mul_toom5(self, a: torch.Tensor, b: torch.Tensor, n: int, reduce: bool, out: torch.Tensor | None = None,
+                  stream=None):
+        """mul_strided through a Toom-5 top level (nine child products per row)."""
+        return self._toom("gf2x_mul_toom5", a, b, n, reduce, out, stream)
+
+    def _toom(self, name, a, b, n, reduce, out, stream):
         if a.dim() != 2 or a.shape != b.shape:
             raise ValueError("a and b must be equal-shaped 2-D tensors")
         _check_operand(a, n, "a")
@@ -337,9 +346,8 @@ class Context:
             out = torch.empty((count, ol), dtype=torch.int64, device=a.device)
         if out.dim() != 2 or out.shape[0] != count or out.shape[1] < ol or not out.is_contiguous():
             raise ValueError("bad output tensor")
-        self._raise(lib().gf2x_mul_toom4(self._h, out.data_ptr(), a.data_ptr(), b.data_ptr(), n, count, a.shape[1],
-                                         out.shape[1], REDUCE if reduce else 0, _stream_handle(stream)),
-                    "gf2x_mul_toom4")
+        self._raise(getattr(lib(), name)(self._h, out.data_ptr(), a.data_ptr(), b.data_ptr(), n, count, a.shape[1],
+                                         out.shape[1], REDUCE if reduce else 0, _stream_handle(stream)), name)
         return out
 
     def mulmod_sparse(self, a: torch.Tensor, pos: torch.Tensor, n: int, out: torch.Tensor | None = None,

@@ -1,7 +1,8 @@
-"""Toom-4 top level (gf2x_mul_toom4): every row equals the product of the
-regular path (gf2x_mul_strided) bit for bit, and the oracle's on samples,
-full and reduced, from one-word operands up to n = 131072, with garbage
-above n, padded strides, and batches larger than one scratch group."""
+"""Toom-4 and Toom-5 top levels (gf2x_mul_toom4, gf2x_mul_toom5): every row
+equals the product of the regular path (gf2x_mul_strided) bit for bit, and
+the oracle's on samples, full and reduced, from one-word operands up to
+n = 131072, with garbage above n, padded strides, and batches larger than
+one scratch group."""
 import numpy as np
 import pytest
 import torch
@@ -17,7 +18,8 @@ pytestmark = pytest.mark.gpu
     (1, 3), (33, 3), (129, 5), (257, 4), (4096, 9), (17669, 37), (57637, 5), (100000, 3), (131072, 3),
 ])
 @pytest.mark.parametrize("reduce", [False, True])
-def test_matches_regular_path_and_oracle(n, count, reduce):
+@pytest.mark.parametrize("k", [4, 5])
+def test_matches_regular_path_and_oracle(n, count, reduce, k):
     from paper_2201_10473_gb300 import Context
     ctx = Context(0)
     try:
@@ -25,7 +27,7 @@ def test_matches_regular_path_and_oracle(n, count, reduce):
         a_g = a.copy()
         if n % 64:                                     # bits above n must be ignored
             a_g[:, -1] |= ~np.uint64((1 << (n % 64)) - 1)
-        got = ctx.mul_toom4(to_dev(a_g), to_dev(b), n, reduce)
+        got = getattr(ctx, f"mul_toom{k}")(to_dev(a_g), to_dev(b), n, reduce)
         ref = ctx.mul_strided(to_dev(a), to_dev(b), n, reduce, persistent=True)
         ctx.sync_status()
         assert torch.equal(got, ref)
@@ -37,7 +39,8 @@ def test_matches_regular_path_and_oracle(n, count, reduce):
         ctx.close()
 
 
-def test_padded_strides():
+@pytest.mark.parametrize("k", [4, 5])
+def test_padded_strides(k):
     from paper_2201_10473_gb300 import Context, gf2x
     n, count = 24659, 6
     L = wl.limbs(n)
@@ -47,7 +50,7 @@ def test_padded_strides():
         pad = np.full((count, 3), np.uint64(0x3C3C3C3C3C3C3C3C))
         da, db = to_dev(np.concatenate([a, pad], 1)), to_dev(np.concatenate([b, pad], 1))
         out = torch.full((count, L + 2), -1, dtype=torch.int64, device="cuda")
-        st = gf2x.lib().gf2x_mul_toom4(ctx._h, out.data_ptr(), da.data_ptr(), db.data_ptr(), n, count, L + 3, L + 2,
+        st = getattr(gf2x.lib(), f"gf2x_mul_toom{k}")(ctx._h, out.data_ptr(), da.data_ptr(), db.data_ptr(), n, count, L + 3, L + 2,
                                        gf2x.REDUCE, None)
         assert st == 0
         torch.cuda.synchronize()
@@ -59,16 +62,17 @@ def test_padded_strides():
         ctx.close()
 
 
-def test_batch_larger_than_one_scratch_group():
-    """At n = 131072 a product needs 115 KiB of scratch: 2400 products run as
-    two groups of the 256 MiB buffer."""
+@pytest.mark.parametrize("k", [4, 5])
+def test_batch_larger_than_one_scratch_group(k):
+    """At n = 131072 a product needs 115 KB (Toom-4) or 119 KB (Toom-5) of
+    scratch: 2400 products run as two groups of the 256 MiB buffer."""
     from paper_2201_10473_gb300 import Context
     n, count = 131072, 2400
     ctx = Context(0)
     try:
         a, b = wl.dense_pair(9992, n, count)
-        got = to_host(ctx.mul_toom4(to_dev(a), to_dev(b), n, True))
-        for p in (0, 2327, 2328, count - 1):
+        got = to_host(getattr(ctx, f"mul_toom{k}")(to_dev(a), to_dev(b), n, True))
+        for p in (0, 1000, 2327, 2328, count - 1):
             assert np.array_equal(got[p], oracle.mulmod(a[p], b[p], n)), p
     finally:
         ctx.close()
