@@ -48,6 +48,16 @@ def test_binding_flags_match_the_header():
     assert len(set(batch)) == len(batch) and all(v & (v - 1) == 0 for v in batch)   # distinct single bits
 
 
+def test_entries_reject_a_null_context_without_a_gpu():
+    L = gf2x.lib()
+    assert L.gf2x_mul_unbalanced(None, None, None, 100, 2, None, 50, 1, 1, 3, None) == 1
+    assert L.gf2x_mulmod_sparse(None, None, None, None, 3, 100, 1, 2, 3, 2, None) == 1
+    assert L.gf2x_mul_toom4(None, None, None, None, 100, 1, 2, 4, 0, None) == 1
+    assert L.gf2x_mul_toom5(None, None, None, None, 100, 1, 2, 4, 0, None) == 1
+    assert L.gf2x_mul_strided(None, None, None, None, 100, 1, 2, 4, 0, gf2x.BATCH_SHARED_A, None) == 1
+    assert L.gf2x_sparse_info_get(100, None) == 1
+
+
 def test_status_strings_and_version():
     L = gf2x.lib()
     assert L.gf2x_status_str(0) == b"ok"
