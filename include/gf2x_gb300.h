@@ -305,8 +305,9 @@ gf2x_status gf2x_mulmod_sparse(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a, co
 
 /* `count` products of one size n through a Toom-4 top level (Toom-Cook
  * 4-7, the next member of Sec. 3's Toom-Cook family after Toom-3; in the
- * size ranges of gf2x quoted in Table tab:compToom it takes over from
- * Toom-3 above degree 22143, with a "gray zone" where the two are close).  Same
+ * size ranges of gf2x listed in the Toom-Cook complexity table of Sec. 3.1
+ * it takes over from Toom-3 above degree 22143, after a band of sizes where
+ * the two cost about the same).  Same
  * operands, strides, flags (GF2X_REDUCE) and results as gf2x_mul_strided.
  * Each operand is cut into four parts of m = ceil(ceil(n/32)/4) 32-bit
  * words and evaluated at 0, 1, x, x+1, x^2, x^2+1 and inf with x = X^32
@@ -320,8 +321,8 @@ gf2x_status gf2x_mul_toom4(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, cons
                            size_t count, size_t stride_in, size_t stride_out, uint32_t flags, gf2x_stream stream);
 
 /* The same through a Toom-5 top level (Toom-Cook 5-9, the next range of
- * Table tab:compToom): five parts of m = ceil(ceil(n/32)/5) words, nine
- * points (those of gf2x_mul_toom4 plus x^2+x and x^2+x+1, whose
+ * the Toom-Cook complexity table of Sec. 3.1): five parts of
+ * m = ceil(ceil(n/32)/5) words, nine points (those of gf2x_mul_toom4 plus x^2+x and x^2+x+1, whose
  * differences again factor into x, x+1 and x^2+x+1), nine child products of
  * E = m + 8 (even) words; scratch 144 E bytes per product. */
 gf2x_status gf2x_mul_toom5(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n,
@@ -365,11 +366,13 @@ gf2x_status gf2x_ctx_sync_status(gf2x_ctx *ctx, gf2x_stream stream);
 const char *gf2x_ctx_last_error(gf2x_ctx *ctx);
 
 /* ---- Products with no allocation at all ----------------------------------
- * The paper has no counterpart to this entry point; it exists for callers
- * that must not allocate device memory: code that runs while a CUDA stream
- * is being captured into a graph (cudaMalloc is not allowed there), code
- * under a fixed memory budget or a no-allocation-after-start-up rule, and
- * hosts that hand the library device buffers but no allocator.
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot call cudaMalloc: a host program whose framework owns all device
+ * memory through its own allocator (memory taken behind its back breaks its
+ * accounting), a service that reserves its whole memory budget at start-up
+ * and must not grow afterwards, and code that must not stall other streams
+ * (cudaMalloc and cudaFree may synchronize the device).  Such callers can
+ * hand the library their operand and result buffers, but no scratch.
  *
  * gf2x_mul_strided_static computes the same `count` products as
  * gf2x_mul_strided (same operand/result layout, strides in limbs, flags
@@ -377,19 +380,25 @@ const char *gf2x_ctx_last_error(gf2x_ctx *ctx);
  * picks the split plan with the fewest modelled operations for n), and needs
  * no context.  Its scratch is a file-scope device array of
  * GF2X_STATIC_SCRATCH_BYTES that every GPU which loads the library holds
- * until the process exits; its two plans live in a second such array.  It
- * calls no cudaMalloc, cudaFree or other allocating routine.
+ * until the process exits; its two plans live in a second such array,
+ * written by a one-block kernel that receives them as launch parameters.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.
  *  - Set-up: the first call on a device (with that device current) looks up
- *    the arrays' device addresses and sets the kernels' shared-memory limits;
- *    make that first call before any stream capture.
+ *    the arrays' device addresses (cudaGetSymbolAddress) and sets the
+ *    kernels' shared-memory limits; make that first call before any stream
+ *    capture.
  *  - Limit: count x gf2x_plan_info.scratch_bytes of the plan must not exceed
  *    GF2X_STATIC_SCRATCH_BYTES, else GF2X_EUNSUPPORTED (split the batch).
  *  - Sharing: every call uses the same arrays, which keep the last call's
- *    contents (nothing in them needs to start at zero); calls whose work
- *    overlaps on the GPU (other streams, other host threads) race — order
- *    them on one stream.
+ *    contents (nothing in them needs to start at zero: every word of the
+ *    scratch is written before it is read); calls whose work overlaps on the
+ *    GPU (other streams, other host threads) race -- order them on one
+ *    stream.
  *  - Errors: GF2X_EINVAL for bad pointers, overlap, flags or a spec that is
- *    not a split plan; launch failures as GF2X_ECUDA. */
+ *    not a split plan; launch failures as GF2X_ECUDA.  There is no context
+ *    and so no error word: the kernels' own refusal of a plan that does not
+ *    match their launch is not reported, and cannot arise here, because the
+ *    plans are built on the host for this very launch. */
 #define GF2X_STATIC_SCRATCH_BYTES (4u << 20)
 
 gf2x_status gf2x_mul_strided_static(uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n, size_t count,

@@ -6,7 +6,7 @@ the chain rule written out term by term; Adam as defined by Kingma & Ba
 Parameter layout: W1 [H x D] row-major, b1 [H], w2 [H], b2 [1].
 
 Pinned in tests/test_mlp_oracle.py by central finite differences, closed
-forms (zero weights, a single active unit) and one hand-computed Adam step.
+forms (zero weights, a single active unit) and hand-computed Adam steps 1-3.
 """
 from __future__ import annotations
 

@@ -925,6 +925,7 @@ static gf2x_status run_toom(gf2x_ctx *ctx, uint32_t K, uint64_t *out, const uint
     t.stride_out = stride_out;
     t.n = n;
     t.flags = flags;
+    t.err = ctx->checked ? ctx->err_dev : nullptr;
     for (size_t c0 = 0; c0 < count; c0 += group) {
         const size_t g = std::min(group, count - c0);
         uint32_t *opnd = reinterpret_cast<uint32_t *>(ctx->ub);

@@ -58,6 +58,7 @@ struct ToomArgs {
     uint32_t m, E, W, OW;     // part words, child operand words, interpolation and product buffer words
     uint32_t *opnd;           // per product 2K - 1 slots of 2E words (A(p_j) | B(p_j))
     const uint32_t *prod;     // per product 2K - 1 child products of 2E words
+    uint32_t *err;            // checked mode: error word for inexact divisions (else null)
 };
 bool toom_shape(uint32_t K, uint32_t n, ToomArgs *a);
 size_t toom_interp_smem(uint32_t K, const ToomArgs &a);

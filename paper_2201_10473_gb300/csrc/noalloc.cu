@@ -30,6 +30,24 @@ struct StaticSetup {
 StaticSetup g_setup[kMaxDevices];
 std::mutex g_setup_mutex;
 
+// Both plans of one call, passed by value as a kernel parameter (3.3 KB,
+// within the 4 KB parameter space): the launch copies them, so no host
+// buffer has to outlive the call.
+struct StaticPlans {
+    GPlan p[2];
+};
+static_assert(sizeof(StaticPlans) <= 4096, "plans must fit the kernel parameter space");
+
+// Writes the call's plans into g_static_plans (named directly: device code
+// may use the array's own name), one 32-bit word per thread.
+__global__ void __launch_bounds__(256) static_plans_kernel(const StaticPlans plans)
+{
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&plans);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(g_static_plans);
+    for (uint32_t w = threadIdx.x; w < sizeof(StaticPlans) / 4; w += blockDim.x)
+        dst[w] = src[w];
+}
+
 // Once per device, with the device current: the arrays' device addresses
 // (the host-side names are stand-ins, not device pointers) and the kernels'
 // dynamic shared-memory limits.
@@ -98,7 +116,8 @@ extern "C" gf2x_status gf2x_mul_strided_static(uint64_t *out, const uint64_t *a,
     } else if (default_split_spec(n, &sp) != GF2X_OK) {
         return GF2X_EUNSUPPORTED;
     }
-    GPlan host[2];
+    StaticPlans sp2;
+    GPlan *host = sp2.p;
     gf2x_plan_info info;
     gf2x_status st = build_plan(n, &sp, &host[0], &info, &host[1]);
     if (st != GF2X_OK)
@@ -113,8 +132,10 @@ extern "C" gf2x_status gf2x_mul_strided_static(uint64_t *out, const uint64_t *a,
     if (st != GF2X_OK)
         return st;
     cudaStream_t s = (cudaStream_t)stream;
-    // pageable source: the copy is staged before the call returns
-    if (cudaMemcpyAsync(su->plans, host, sizeof(host), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    // the plans travel in the upload kernel's parameters, ordered before the
+    // products on the same stream
+    static_plans_kernel<<<1, 256, 0, s>>>(sp2);
+    if (cudaGetLastError() != cudaSuccess)
         return GF2X_ECUDA;
 
     const GPlan &T = host[0], &C = host[1];
@@ -127,7 +148,7 @@ extern "C" gf2x_status gf2x_mul_strided_static(uint64_t *out, const uint64_t *a,
     ta.stride_out = stride_out;
     ta.count = (uint32_t)count;
     ta.mode = kItemsStrided;
-    ta.err = nullptr;
+    ta.err = nullptr;   // no error word: see the header (device refusals cannot arise here)
     if (launch_split_eval(ta, su->scratch, (unsigned)count, T.threads, 4ull * T.smem_words, s) != cudaSuccess)
         return GF2X_ECUDA;
     LaunchArgs ca;

@@ -19,6 +19,12 @@
 // (x^3+1)/(x+1) is a product by 1+x followed by a prefix XOR with a stride
 // of three words.  Every division is exact.  All loops and addresses depend
 // on the sizes only (constant time in the operand bits).
+//
+// Checked mode (a non-null error word): the interpolation verifies every
+// division -- the a words dropped by x^a are zero, each prefix XOR of a
+// division by x+1 ends in a zero word, each division by x^2+x+1 leaves its
+// last three words zero -- and that every C_k fits its 2m words, so that a
+// wrong table entry is reported, not only seen as a wrong product.
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -225,17 +231,42 @@ __global__ void __launch_bounds__(kT4Threads) toom_interp_kernel(const ToomArgs 
                     }
                 num[t] = v;
             }
+            if (args.err) {   // the words the division by x^a drops are zero
+                for (uint32_t t = threadIdx.x; t < I.a; t += blockDim.x) {
+                    uint32_t v = 0;
+                    for (uint32_t j = 0; j < NF; ++j)
+                        for (uint32_t q = 0; q < I.n[j]; ++q)
+                            if (t >= I.e[j][q])
+                                v ^= S[j * W + t - I.e[j][q]];
+                    if (v)
+                        atomicOr(args.err, kErrDivX);
+                }
+            }
             __syncthreads();
-            for (uint32_t u = 0; u < I.b; ++u)
+            for (uint32_t u = 0; u < I.b; ++u) {
                 prefix_xor(num, W, 1u, carry);
+                if (args.err && threadIdx.x == 0 && num[W - 1u])   // remainder by x+1
+                    atomicOr(args.err, kErrDivX1);
+            }
             for (uint32_t u = 0; u < I.c; ++u) {
-                for (uint32_t t = threadIdx.x; t < W; t += blockDim.x)
+                for (uint32_t t = threadIdx.x; t < W; t += blockDim.x) {
                     tmp[t] = num[t] ^ (t >= 1u ? num[t - 1u] : 0u);
+                    if (args.err && t == W - 1u && num[t])   // the product by 1+x must fit W words
+                        atomicOr(args.err, kErrDivX2X1);
+                }
                 __syncthreads();
                 prefix_xor(tmp, W, 3u, carry);
-                for (uint32_t t = threadIdx.x; t < W; t += blockDim.x)
+                for (uint32_t t = threadIdx.x; t < W; t += blockDim.x) {
                     num[t] = tmp[t];
+                    if (args.err && t + 3u >= W && tmp[t])   // remainder by x^3+1
+                        atomicOr(args.err, kErrDivX2X1);
+                }
                 __syncthreads();
+            }
+            if (args.err) {   // C_k is a sum of products of m-word parts: 2m words
+                for (uint32_t t = 2u * m + threadIdx.x; t < W; t += blockDim.x)
+                    if (num[t])
+                        atomicOr(args.err, kErrPad);
             }
             const uint32_t off = (k + 1u) * m;
             for (uint32_t t = threadIdx.x; t < W; t += blockDim.x)

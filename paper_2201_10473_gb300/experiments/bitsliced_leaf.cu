@@ -359,6 +359,33 @@ static void prof_one()
     CK(cudaFree(din)); CK(cudaFree(dout));
 }
 
+#ifdef GF2X_EXPERIMENT_LIB
+// Test entry point (built into libgf2x_exp_bitsliced.so by build.py): one
+// leaf pass over `nctas` groups of 32G leaves of 192 x 192 bits, each leaf
+// LW = 12 words (a: 6 words, b: 6 words; the 12-word product overwrites
+// them in `out`), device pointers, asynchronous on `stream`.  mode 0: the
+// comb (G = 7), 1: bitsliced 3-way/2-way Karatsuba schedule (G = 4),
+// 2: bitsliced diagonal schoolbook (G = 8).  Returns 0 on success.
+extern "C" int gf2x_exp_bitsliced_group(int mode) { return mode == 0 ? 7 : mode == 1 ? 4 : mode == 2 ? 8 : 0; }
+extern "C" int gf2x_exp_bitsliced_leaves(const uint32_t *in, uint32_t *out, int nctas, int mode, void *stream)
+{
+    if (nctas <= 0) return 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mode == 0) {
+        if (cudaFuncSetAttribute(kern<7, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of<7, 0>()) != cudaSuccess) return 1;
+        kern<7, 0><<<nctas, 128, smem_of<7, 0>(), st>>>(in, out, 1);
+    } else if (mode == 1) {
+        if (cudaFuncSetAttribute(kern<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of<4, 1>()) != cudaSuccess) return 1;
+        kern<4, 1><<<nctas, 128, smem_of<4, 1>(), st>>>(in, out, 1);
+    } else if (mode == 2) {
+        if (cudaFuncSetAttribute(kern<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of<8, 2>()) != cudaSuccess) return 1;
+        kern<8, 2><<<nctas, 128, smem_of<8, 2>(), st>>>(in, out, 1);
+    } else {
+        return 2;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+#else
 int main(int argc, char **argv)
 {
     if (argc > 1) {   // one launch of each kind, for a profiler
@@ -376,3 +403,4 @@ int main(int argc, char **argv)
     rc |= check_and_time<8, 2>("diag");
     return rc;
 }
+#endif

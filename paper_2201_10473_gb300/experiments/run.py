@@ -6,7 +6,7 @@ import tempfile
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
-PROGRAMS = ("alu_pipes", "fma_pipes", "mma_pipes", "tc_toeplitz", "bitsliced_leaf")
+PROGRAMS = ("tc_toeplitz", "bitsliced_leaf")
 
 
 def main(argv=None):

@@ -122,6 +122,25 @@ static void clmul_ref(const uint32_t* a, const uint32_t* b, uint32_t* c) {
         if ((a[j >> 5] >> (j & 31)) & 1) c[(i + j) >> 5] ^= 1u << ((i + j) & 31);
 }
 
+#ifdef GF2X_EXPERIMENT_LIB
+// Test entry points (built into libgf2x_exp_tc.so by build.py): `count`
+// full 512 x 512-bit products, operands of 16 words per row, results of 32
+// words per row, device pointers, asynchronous on `stream`.  0 on success.
+extern "C" int gf2x_exp_tc_mul512(const uint32_t* A, const uint32_t* B, uint32_t* C, int count, void* stream) {
+  if (count <= 0) return 0;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) return 1;
+  tc_mul<<<sms * 8, 32 * WARPS, 0, (cudaStream_t)stream>>>(A, B, C, count);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+extern "C" int gf2x_exp_comb_mul512(const uint32_t* A, const uint32_t* B, uint32_t* C, int count, void* stream) {
+  if (count <= 0) return 0;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) return 1;
+  comb_mul<<<sms * 8, 256, 0, (cudaStream_t)stream>>>(A, B, C, count);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+#else
 int main() {
   const int count = 1 << 20;
   std::vector<uint32_t> ha((size_t)count * S), hb((size_t)count * S);
@@ -164,3 +183,4 @@ int main() {
   }
   return 0;
 }
+#endif

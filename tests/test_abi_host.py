@@ -38,6 +38,19 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(L, name), name
 
 
+def test_experiment_libraries_load_and_export_their_test_entries():
+    import ctypes
+
+    from paper_2201_10473_gb300 import build
+    build.build()
+    tc = ctypes.CDLL(build.experiment_lib("libgf2x_exp_tc.so"))
+    assert hasattr(tc, "gf2x_exp_tc_mul512") and hasattr(tc, "gf2x_exp_comb_mul512")
+    bs = ctypes.CDLL(build.experiment_lib("libgf2x_exp_bitsliced.so"))
+    assert hasattr(bs, "gf2x_exp_bitsliced_leaves")
+    bs.gf2x_exp_bitsliced_group.restype = ctypes.c_int
+    assert [bs.gf2x_exp_bitsliced_group(m) for m in range(4)] == [7, 4, 8, 0]
+
+
 def test_binding_flags_match_the_header():
     text = open(os.path.join(ROOT, "include", "gf2x_gb300.h")).read()
     defines = {m.group(1): int(m.group(2), 0) for m in re.finditer(r"#define GF2X_([A-Z_]+)\s+\(?([0-9x]+)u", text)}

@@ -76,3 +76,31 @@ def test_batch_larger_than_one_scratch_group(k):
             assert np.array_equal(got[p], oracle.mulmod(a[p], b[p], n)), p
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("n", [129, 17669, 57637, 131072])
+@pytest.mark.parametrize("k", [4, 5])
+def test_checked_mode_reports_no_violation(n, k):
+    """In checked mode the interpolation kernel verifies every division
+    (dropped words of x^a, the remainders by x+1 and x^2+x+1) and that each
+    coefficient C_k fits its 2m words; correct tables report nothing."""
+    from paper_2201_10473_gb300 import Context
+    ctx = Context(0)
+    try:
+        ctx.set_checked(True)
+        count = 4
+        a, b = wl.dense_pair(9993 + n, n, count)
+        a[0] = np.uint64(0xFFFFFFFFFFFFFFFF)            # all-ones row: every word of every part set
+        b[0] = np.uint64(0xFFFFFFFFFFFFFFFF)
+        if n % 64:
+            a[0, -1] &= np.uint64((1 << (n % 64)) - 1)
+            b[0, -1] &= np.uint64((1 << (n % 64)) - 1)
+        for reduce in (False, True):
+            got = to_host(getattr(ctx, f"mul_toom{k}")(to_dev(a), to_dev(b), n, reduce))
+            ctx.sync_status()                           # raises on a reported violation
+            for p in range(count):
+                exp = oracle.mulmod(a[p], b[p], n) if reduce else oracle.mul(a[p], b[p], n)
+                assert np.array_equal(got[p][: len(exp)], exp), (p, reduce)
+    finally:
+        ctx.set_checked(False)
+        ctx.close()

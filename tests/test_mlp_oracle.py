@@ -54,3 +54,35 @@ def test_adam_first_step_moves_by_lr_times_sign():
     q, m, v = mlp.adam_step(p, g, np.zeros(3), np.zeros(3), 0.1, 0.9, 0.999, 1e-12, 1)
     # with bias correction the first step is lr * g / |g|
     assert np.allclose(q, [0.9, -1.9, 0.0])
+
+
+def test_adam_second_and_third_steps_follow_the_bias_correction():
+    # Hand derivation (Kingma & Ba, Algorithm 1): with zero gradients before
+    # step t and gradient g at step t, the moments are m = (1-b1) g and
+    # v = (1-b2) g^2, so the corrected moments are g / (1 + b1 + ... + b1^(t-1))
+    # and g^2 / (1 + b2 + ... + b2^(t-1)) and the step is
+    #   lr sign(g) sqrt(1 + b2 + ... + b2^(t-1)) / (1 + b1 + ... + b1^(t-1)).
+    # With b1 = 0.9, b2 = 0.999: t = 2 gives sqrt(1.999) / 1.9 = 0.7441368...,
+    # t = 3 gives sqrt(2.997001) / 2.71 = 0.6388136...  A correction by
+    # beta**1 at every step would give 1.0 and 0.964...; no correction 3.16.
+    lr, b1, b2 = 0.1, 0.9, 0.999
+    for t, expect in ((2, 0.7441368), (3, 0.6388136)):
+        p = np.array([1.0, 1.0])
+        m = np.zeros(2)
+        v = np.zeros(2)
+        for step in range(1, t + 1):
+            g = np.array([0.25, -4.0]) if step == t else np.zeros(2)
+            p, m, v = mlp.adam_step(p, g, m, v, lr, b1, b2, 0.0 if step == t else 1.0, step)
+        assert np.allclose(p, [1.0 - lr * expect, 1.0 + lr * expect], rtol=0, atol=1e-7), (t, p)
+
+
+def test_adam_two_steps_with_nonzero_history():
+    # b1 = b2 = 0.5, lr = 1, eps = 0, g1 = 2 then g2 = 4 (worked by hand):
+    # step 1: m = 1, v = 2, corrected 2 and 4, step 2 / 2 = 1     -> p = -1
+    # step 2: m = 0.5 + 2 = 2.5, v = 1 + 8 = 9; corrections 1 - 0.25 = 0.75
+    # for both: m^ = 10/3, v^ = 12, step (10/3) / sqrt(12) = 0.9622504 -> p = -1.9622504
+    p, m, v = mlp.adam_step(np.array([0.0]), np.array([2.0]), np.zeros(1), np.zeros(1), 1.0, 0.5, 0.5, 0.0, 1)
+    assert np.allclose(p, [-1.0]) and np.allclose(m, [1.0]) and np.allclose(v, [2.0])
+    p, m, v = mlp.adam_step(p, np.array([4.0]), m, v, 1.0, 0.5, 0.5, 0.0, 2)
+    assert np.allclose(m, [2.5]) and np.allclose(v, [9.0])
+    assert np.allclose(p, [-1.9622504], rtol=0, atol=1e-7)

@@ -1,8 +1,9 @@
 """gf2x_mul_strided_static: the entry point for callers that cannot allocate
-device memory (inside a stream capture, under a no-allocation rule, or with
-no allocator of their own).  It must give exactly what gf2x_mul_strided gives
-with the same split plan, call after call, although its scratch is one
-shared file-scope device array.  Collected last (file name) so that a run
+device memory (a framework that owns every device allocation, a service with
+a budget fixed at start-up, code that must not let cudaMalloc synchronize the
+device).  Call after call it must give exactly what gf2x_mul_strided gives
+with the same split plan, and the oracle's products, although its scratch is
+one shared file-scope device array.  Collected last (file name) so that a run
 stopping at the first failure has already run every other test; it passes
 alone in a fresh process too."""
 import ctypes
@@ -11,8 +12,9 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import workloads as wl
-from gpu_util import to_dev
+from gpu_util import first_diff, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +58,9 @@ def test_static_entry_matches_strided_entry_twice(n, spec, count, reduce):
             assert st == 0, st
             torch.cuda.synchronize()
             assert torch.equal(got, ref), (n, call)   # bit-exact, as every other parity test
+            exp = oracle.mul_batch(a, b, n, reduce=reduce)
+            g = to_host(got)
+            assert np.array_equal(g, exp), (n, call, first_diff(g, exp))
     finally:
         ctx.close()
 
