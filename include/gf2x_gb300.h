@@ -41,7 +41,7 @@ extern "C" {
 typedef enum {
     GF2X_OK = 0,
     GF2X_EINVAL = 1,        /* bad pointer, overlap, bad flag or bad plan spec */
-    GF2X_ENOMEM = 2,        /* a context allocation failed */
+    GF2X_ENOMEM = 2,        /* an allocation failed, or a fixed workspace is too small */
     GF2X_ECUDA = 3,         /* a CUDA runtime call failed */
     GF2X_ETIMEOUT = 4,      /* a bounded wait ran out */
     GF2X_EUNSUPPORTED = 5,  /* n outside [1, GF2X_MAX_N] or a plan that does not fit */
@@ -147,10 +147,36 @@ gf2x_status gf2x_plan_info_get(uint32_t n, const gf2x_plan_spec *spec, gf2x_plan
 gf2x_status gf2x_spec_parse(const char *text, gf2x_plan_spec *spec);
 
 /* Create a context on CUDA device `device` (made current on the calling
- * thread).  The context owns device-side plan tables and item staging
- * buffers; it allocates nothing in the compute calls afterwards except when
- * a batch outgrows its staging buffers. */
-gf2x_status gf2x_ctx_create(gf2x_ctx **ctx, int device);
+ * thread).  The context owns device-side plan tables, item staging buffers
+ * and scratch.
+ *  - workspace_bytes = 0: scratch grows on demand -- the split-plan scratch,
+ *    the unbalanced/Toom scratch, the host-buffer pipeline and the item
+ *    staging are allocated (cudaMalloc / cudaMallocHost, which synchronize)
+ *    by the first compute call that needs more.
+ *  - workspace_bytes > 0: one device arena of that size (rounded down to
+ *    1 KiB) is allocated here -- half split-plan scratch, a quarter
+ *    unbalanced/Toom scratch, a quarter host-buffer pipeline -- with 4 x
+ *    16384 item staging slots, and NO compute call allocates afterwards:
+ *    batches run in chunks that fit, host item batches above 16384 items run
+ *    in pieces (each piece ordered and grouped by itself), and a call whose
+ *    single product does not fit returns GF2X_ENOMEM.
+ *  - plan_db_path: a plan database to install (see gf2x_ctx_load_plan_db;
+ *    the batch bucket nearest to 4096 is used), or NULL for default plans.
+ * Errors: GF2X_ENOMEM when an allocation fails, GF2X_ECUDA for another CUDA
+ * failure, the plan database's status when it is rejected (no context is
+ * returned then). */
+gf2x_status gf2x_ctx_create(gf2x_ctx **ctx, int device, size_t workspace_bytes, const char *plan_db_path);
+
+/* Allocations the context has made since it was created (cudaMalloc and
+ * cudaMallocHost calls, creation included) and their bytes; either pointer
+ * may be NULL.  With a fixed workspace the count stays at its value after
+ * gf2x_ctx_create.  Host only. */
+gf2x_status gf2x_ctx_alloc_count(gf2x_ctx *ctx, uint64_t *allocations, uint64_t *bytes);
+
+/* For tests of the GF2X_ENOMEM paths: the next `count` device or pinned
+ * allocations of any context fail as if the memory were exhausted (no CUDA
+ * call is made for them).  Returns the previous count.  Process-wide. */
+uint32_t gf2x_debug_fail_next_allocs(uint32_t count);
 
 /* Release everything the context owns (waits for its work to finish). */
 void gf2x_ctx_destroy(gf2x_ctx *ctx);
@@ -360,6 +386,12 @@ gf2x_status gf2x_ctx_launch_shape(gf2x_ctx *ctx, uint32_t n, uint32_t *threads, 
 /* Wait for `stream`, then report and clear any checked-mode violation
  * (GF2X_EDEVICE) or asynchronous CUDA error (GF2X_ECUDA). */
 gf2x_status gf2x_ctx_sync_status(gf2x_ctx *ctx, gf2x_stream stream);
+
+/* gf2x_ctx_sync_status with a deadline: polls the stream every 50 us (no
+ * blocking synchronize) for at most timeout_ms; GF2X_ETIMEOUT if its work
+ * has not finished by then (the work goes on; wait again or destroy the
+ * context, which waits), else the result of gf2x_ctx_sync_status. */
+gf2x_status gf2x_ctx_wait(gf2x_ctx *ctx, gf2x_stream stream, uint32_t timeout_ms);
 
 /* Text of the last error recorded in the context (static until the next
  * call on it). */

@@ -4,12 +4,15 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -31,6 +34,11 @@ struct PlanEntry {
 };
 
 constexpr uint64_t kWorkspaceCap = 256ull << 20;  // split plans run in chunks of at most this much scratch
+constexpr size_t kFixedStagingItems = 16384;      // item staging per ring buffer in a fixed-workspace context
+
+// Allocation failures injected on the host (tests of the GF2X_ENOMEM paths):
+// the next g_fail_allocs allocations of any context fail without a CUDA call.
+std::atomic<uint32_t> g_fail_allocs{0};
 
 struct Staging {
     DevItem *host = nullptr;   // pinned
@@ -86,7 +94,51 @@ struct gf2x_ctx {
     cudaEvent_t ub_done = nullptr;                      // recorded after the last use of ub
     cudaStream_t ub_stream = nullptr;
     bool ub_used = false;
+    bool fixed = false;                                 // workspace fixed at creation: compute calls allocate nothing
+    void *arena = nullptr;                              // the fixed workspace (split | unbalanced/Toom | host pipeline)
+    uint64_t allocs = 0;                                // device and pinned allocations made by the context
+    uint64_t alloc_bytes = 0;
 };
+
+// Every device or pinned allocation of a context goes through these two
+// (counted; failures injectable by gf2x_debug_fail_next_allocs).
+static bool injected_failure()
+{
+    uint32_t v = g_fail_allocs.load();
+    while (v > 0 && !g_fail_allocs.compare_exchange_weak(v, v - 1)) {
+    }
+    return v > 0;
+}
+
+static cudaError_t ctx_malloc(gf2x_ctx *ctx, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (injected_failure())
+        return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) {
+        ctx->allocs++;
+        ctx->alloc_bytes += bytes;
+    } else {
+        *p = nullptr;
+    }
+    return e;
+}
+
+static cudaError_t ctx_malloc_host(gf2x_ctx *ctx, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (injected_failure())
+        return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMallocHost(p, bytes);
+    if (e == cudaSuccess) {
+        ctx->allocs++;
+        ctx->alloc_bytes += bytes;
+    } else {
+        *p = nullptr;
+    }
+    return e;
+}
 
 static std::string plan_key(uint32_t n, const gf2x_plan_spec &spec, int checked)
 {
@@ -137,7 +189,7 @@ extern "C" gf2x_status gf2x_plan_info_get(uint32_t n, const gf2x_plan_spec *spec
 
 extern "C" gf2x_status gf2x_spec_parse(const char *text, gf2x_plan_spec *spec) { return parse_spec(text, spec); }
 
-extern "C" gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
+extern "C" gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device, size_t workspace_bytes, const char *plan_db_path)
 {
     if (!out)
         return GF2X_EINVAL;
@@ -151,22 +203,50 @@ extern "C" gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
         return GF2X_ECUDA;
     }
     ctx->device = device;
+    bool oom = false;   // an allocation (not another CUDA call) failed
+    auto alloc = [&](void **p, size_t bytes, bool host) {
+        if (e != cudaSuccess)
+            return;
+        e = host ? ctx_malloc_host(ctx, p, bytes) : ctx_malloc(ctx, p, bytes);
+        oom = e == cudaErrorMemoryAllocation;
+    };
     e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
-    if (e == cudaSuccess)
-        e = cudaMallocHost((void **)&ctx->plans_host, sizeof(GPlan) * kPlanCapacity);
-    if (e == cudaSuccess)
-        e = cudaMalloc((void **)&ctx->plans_dev, sizeof(GPlan) * kPlanCapacity);
-    if (e == cudaSuccess)
-        e = cudaMalloc((void **)&ctx->err_dev, sizeof(uint32_t));
+    alloc((void **)&ctx->plans_host, sizeof(GPlan) * kPlanCapacity, true);
+    alloc((void **)&ctx->plans_dev, sizeof(GPlan) * kPlanCapacity, false);
+    alloc((void **)&ctx->err_dev, sizeof(uint32_t), false);
     if (e == cudaSuccess)
         e = cudaMemset(ctx->err_dev, 0, sizeof(uint32_t));
-    if (e == cudaSuccess)
-        e = cudaMallocHost((void **)&ctx->plan_of_n_host, sizeof(uint32_t) * (GF2X_MAX_N + 1));
-    if (e == cudaSuccess)
-        e = cudaMalloc((void **)&ctx->plan_of_n_dev, sizeof(uint32_t) * (GF2X_MAX_N + 1));
+    alloc((void **)&ctx->plan_of_n_host, sizeof(uint32_t) * (GF2X_MAX_N + 1), true);
+    alloc((void **)&ctx->plan_of_n_dev, sizeof(uint32_t) * (GF2X_MAX_N + 1), false);
     if (e == cudaSuccess) {
         memset(ctx->plan_of_n_host, 0xff, sizeof(uint32_t) * (GF2X_MAX_N + 1));
         e = cudaMemset(ctx->plan_of_n_dev, 0xff, sizeof(uint32_t) * (GF2X_MAX_N + 1));
+    }
+    if (workspace_bytes > 0 && e == cudaSuccess) {
+        // one arena: half for split-plan scratch, a quarter for the
+        // unbalanced / Toom scratch, a quarter for the host-buffer pipeline
+        // (they may be live at the same time: a host-buffer or Toom call runs
+        // split plans inside it)
+        const size_t W = workspace_bytes & ~(size_t)1023;
+        alloc(&ctx->arena, W, false);
+        if (e == cudaSuccess) {
+            uint8_t *base = static_cast<uint8_t *>(ctx->arena);
+            ctx->ws = reinterpret_cast<uint32_t *>(base);
+            ctx->ws_bytes = W / 2;
+            ctx->ub = reinterpret_cast<uint64_t *>(base + W / 2);
+            ctx->ub_bytes = W / 4;
+            ctx->hp.buf = reinterpret_cast<uint64_t *>(base + W / 2 + W / 4);
+            ctx->hp.bytes = W / 4;
+            ctx->fixed = true;
+        }
+        for (auto &r : ctx->ring) {
+            alloc((void **)&r.host, kFixedStagingItems * sizeof(DevItem), true);
+            alloc((void **)&r.dev, kFixedStagingItems * sizeof(DevItem), false);
+            if (e == cudaSuccess)
+                r.cap = kFixedStagingItems;
+        }
+        ctx->scratch_items.reserve(kFixedStagingItems);
+        ctx->scratch_S.reserve(kFixedStagingItems);
     }
     if (e == cudaSuccess)
         e = cudaDeviceSynchronize();
@@ -177,12 +257,51 @@ extern "C" gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device)
         e = prepare_split();
     if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&ctx->ws_done, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&ctx->ub_done, cudaEventDisableTiming);
+    for (auto &r : ctx->ring)
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) {   // streams and events of the host-buffer pipeline
+        HostPipe &hp = ctx->hp;
+        e = cudaStreamCreateWithFlags(&hp.h2d, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithFlags(&hp.d2h, cudaStreamNonBlocking);
+        cudaEvent_t *evs[] = {&hp.entry, &hp.in[0], &hp.in[1], &hp.done[0], &hp.done[1], &hp.out[0], &hp.out[1]};
+        for (cudaEvent_t *ev : evs)
+            if (e == cudaSuccess)
+                e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        hp.ready = e == cudaSuccess;
+    }
     if (e != cudaSuccess) {
         gf2x_ctx_destroy(ctx);
-        return GF2X_ECUDA;
+        return oom ? GF2X_ENOMEM : GF2X_ECUDA;
+    }
+    if (plan_db_path) {
+        gf2x_status st = gf2x_ctx_load_plan_db(ctx, plan_db_path, 4096);
+        if (st != GF2X_OK) {
+            gf2x_ctx_destroy(ctx);
+            return st;
+        }
     }
     *out = ctx;
     return GF2X_OK;
+}
+
+extern "C" gf2x_status gf2x_ctx_alloc_count(gf2x_ctx *ctx, uint64_t *allocations, uint64_t *bytes)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    if (allocations)
+        *allocations = ctx->allocs;
+    if (bytes)
+        *bytes = ctx->alloc_bytes;
+    return GF2X_OK;
+}
+
+extern "C" uint32_t gf2x_debug_fail_next_allocs(uint32_t count)
+{
+    return g_fail_allocs.exchange(count);
 }
 
 extern "C" void gf2x_ctx_destroy(gf2x_ctx *ctx)
@@ -209,17 +328,21 @@ extern "C" void gf2x_ctx_destroy(gf2x_ctx *ctx)
         cudaFreeHost(ctx->plan_of_n_host);
     if (ctx->plan_of_n_dev)
         cudaFree(ctx->plan_of_n_dev);
-    if (ctx->ws)
-        cudaFree(ctx->ws);
+    if (ctx->arena) {   // ws, ub and hp.buf live in it
+        cudaFree(ctx->arena);
+    } else {
+        if (ctx->ws)
+            cudaFree(ctx->ws);
+        if (ctx->ub)
+            cudaFree(ctx->ub);
+        if (ctx->hp.buf)
+            cudaFree(ctx->hp.buf);
+    }
     if (ctx->ws_done)
         cudaEventDestroy(ctx->ws_done);
-    if (ctx->ub)
-        cudaFree(ctx->ub);
     if (ctx->ub_done)
         cudaEventDestroy(ctx->ub_done);
     HostPipe &hp = ctx->hp;
-    if (hp.buf)
-        cudaFree(hp.buf);
     for (cudaStream_t st : {hp.h2d, hp.d2h})
         if (st)
             cudaStreamDestroy(st);
@@ -460,6 +583,8 @@ static gf2x_status ensure_workspace(gf2x_ctx *ctx, size_t bytes)
 {
     if (ctx->ws_bytes >= bytes)
         return GF2X_OK;
+    if (ctx->fixed)   // chunks shrink to the fixed scratch; only one product that does not fit fails
+        return fail(ctx, GF2X_ENOMEM, "fixed workspace too small for one product of this split plan");
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "workspace wait");
@@ -467,7 +592,7 @@ static gf2x_status ensure_workspace(gf2x_ctx *ctx, size_t bytes)
         cudaFree(ctx->ws);
     ctx->ws = nullptr;
     ctx->ws_bytes = 0;
-    if (cudaMalloc((void **)&ctx->ws, bytes) != cudaSuccess)
+    if (ctx_malloc(ctx, (void **)&ctx->ws, bytes) != cudaSuccess)
         return fail(ctx, GF2X_ENOMEM, "split workspace allocation");
     ctx->ws_bytes = bytes;
     return GF2X_OK;
@@ -536,7 +661,7 @@ static gf2x_status run_split_args(gf2x_ctx *ctx, uint32_t top_slot, const Launch
 {
     const GPlan &T = ctx->plans_host[top_slot];
     const size_t per = 4ull * T.lev[0].nch * 2ull * T.lev[0].E;
-    const size_t want = std::max<size_t>(per, std::min<size_t>(count * per, kWorkspaceCap / per * per));
+    const size_t want = ctx->fixed ? per : std::max<size_t>(per, std::min<size_t>(count * per, kWorkspaceCap / per * per));
     gf2x_status st = ensure_workspace(ctx, want);
     if (st != GF2X_OK)
         return st;
@@ -671,9 +796,17 @@ static gf2x_status strided_on_slot(gf2x_ctx *ctx, uint32_t slot, uint64_t *out, 
 // bytes (grows only; cudaFree synchronizes the device, so no call still
 // uses the old buffer), ordered after the previous call that used it when
 // that came on another stream.  scratch_release records the ordering event.
+// Bytes of that scratch one call may use per group of products.
+static size_t scratch_cap(const gf2x_ctx *ctx)
+{
+    return ctx->fixed ? ctx->ub_bytes : (size_t)kWorkspaceCap;
+}
+
 static gf2x_status scratch_acquire(gf2x_ctx *ctx, size_t want, cudaStream_t s)
 {
     if (ctx->ub_bytes < want) {
+        if (ctx->fixed)
+            return fail(ctx, GF2X_ENOMEM, "fixed workspace too small for one product of this call");
         if (ctx->ub) {
             cudaError_t e = cudaFree(ctx->ub);
             ctx->ub = nullptr;
@@ -681,19 +814,12 @@ static gf2x_status scratch_acquire(gf2x_ctx *ctx, size_t want, cudaStream_t s)
             if (e != cudaSuccess)
                 return cuda_fail(ctx, e, "scratch");
         }
-        cudaError_t e = cudaMalloc((void **)&ctx->ub, want);
+        cudaError_t e = ctx_malloc(ctx, (void **)&ctx->ub, want);
         if (e != cudaSuccess) {
             ctx->ub = nullptr;
             return e == cudaErrorMemoryAllocation ? fail(ctx, GF2X_ENOMEM, "scratch") : cuda_fail(ctx, e, "scratch");
         }
         ctx->ub_bytes = want;
-    }
-    if (!ctx->ub_done) {
-        cudaError_t e = cudaEventCreateWithFlags(&ctx->ub_done, cudaEventDisableTiming);
-        if (e != cudaSuccess) {
-            ctx->ub_done = nullptr;
-            return cuda_fail(ctx, e, "scratch event");
-        }
     }
     if (ctx->ub_used && ctx->ub_stream != s) {
         cudaError_t e = cudaStreamWaitEvent(s, ctx->ub_done, 0);
@@ -802,7 +928,7 @@ extern "C" gf2x_status gf2x_mul_unbalanced(gf2x_ctx *ctx, uint64_t *out, const u
         step = Wp;
     // scratch per product: chunks x (two operand rows + one product row)
     const size_t per = 8ull * chunks * (2ull * Ld + Wp);
-    const size_t group = std::max<size_t>(1, std::min<size_t>(count, kWorkspaceCap / per));
+    const size_t group = std::max<size_t>(1, std::min<size_t>(count, scratch_cap(ctx) / per));
     gf2x_status sst = scratch_acquire(ctx, group * per, s);
     if (sst != GF2X_OK)
         return sst;
@@ -917,7 +1043,7 @@ static gf2x_status run_toom(gf2x_ctx *ctx, uint32_t K, uint64_t *out, const uint
     if (st != GF2X_OK)
         return st;
     const size_t per = 4ull * 4u * NP * t.E;   // NP operand slots and NP products of 2E words
-    const size_t group = std::max<size_t>(1, std::min<size_t>(count, kWorkspaceCap / per));
+    const size_t group = std::max<size_t>(1, std::min<size_t>(count, scratch_cap(ctx) / per));
     st = scratch_acquire(ctx, group * per, s);
     if (st != GF2X_OK)
         return st;
@@ -979,18 +1105,10 @@ static gf2x_status host_pipe_ready(gf2x_ctx *ctx, size_t bytes)
 {
     HostPipe &hp = ctx->hp;
     cudaError_t e = cudaSuccess;
-    if (!hp.ready) {
-        e = cudaStreamCreateWithFlags(&hp.h2d, cudaStreamNonBlocking);
-        if (e == cudaSuccess)
-            e = cudaStreamCreateWithFlags(&hp.d2h, cudaStreamNonBlocking);
-        cudaEvent_t *evs[] = {&hp.entry, &hp.in[0], &hp.in[1], &hp.done[0], &hp.done[1], &hp.out[0], &hp.out[1]};
-        for (cudaEvent_t *ev : evs)
-            if (e == cudaSuccess)
-                e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
-        if (e != cudaSuccess)
-            return cuda_fail(ctx, e, "host pipeline set-up");
-        hp.ready = true;
-    }
+    if (!hp.ready)
+        return fail(ctx, GF2X_ECUDA, "host pipeline streams missing");
+    if (bytes > hp.bytes && ctx->fixed)
+        return fail(ctx, GF2X_ENOMEM, "fixed workspace too small for one product of the host pipeline");
     if (bytes > hp.bytes) {
         if (hp.buf) {
             e = cudaFree(hp.buf);   // synchronizes the device: no copy or product still uses it
@@ -999,7 +1117,7 @@ static gf2x_status host_pipe_ready(gf2x_ctx *ctx, size_t bytes)
             if (e != cudaSuccess)
                 return cuda_fail(ctx, e, "host pipeline buffers");
         }
-        e = cudaMalloc((void **)&hp.buf, bytes);
+        e = ctx_malloc(ctx, (void **)&hp.buf, bytes);
         if (e != cudaSuccess) {
             hp.buf = nullptr;
             return e == cudaErrorMemoryAllocation ? fail(ctx, GF2X_ENOMEM, "host pipeline buffers")
@@ -1030,7 +1148,9 @@ extern "C" gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const
     // host strides (a single row may have any stride); the device rows are packed
     const size_t hi = count > 1 ? stride_in : L, ho = count > 1 ? stride_out : Lo;
     const size_t nchunk = count >= 2048 ? 4 : (count >= 512 ? 2 : 1);
-    const size_t K = (count + nchunk - 1) / nchunk;
+    size_t K = (count + nchunk - 1) / nchunk;
+    if (ctx->fixed)   // as many products per chunk as two buffer sets in the fixed workspace hold
+        K = std::min(K, std::max<size_t>(1, ctx->hp.bytes / (2 * 8 * (2 * L + Lo))));
     const size_t in_w = K * L, set_w = 2 * in_w + K * Lo;
     st = host_pipe_ready(ctx, 2 * set_w * sizeof(uint64_t));
     if (st != GF2X_OK)
@@ -1079,7 +1199,7 @@ extern "C" gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const
             return cuda_fail(ctx, e, "host pipeline copy out");
     }
     e = cudaStreamWaitEvent(s, hp.out[0], 0);
-    if (e == cudaSuccess && nchunk > 1)
+    if (e == cudaSuccess && count > K)
         e = cudaStreamWaitEvent(s, hp.out[1], 0);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "host pipeline completion");
@@ -1099,6 +1219,8 @@ static gf2x_status take_staging(gf2x_ctx *ctx, size_t count, Staging **out)
         r.pending = false;
     }
     if (r.cap < count) {
+        if (ctx->fixed)
+            return fail(ctx, GF2X_ENOMEM, "batch larger than the fixed item staging");
         size_t cap = std::max<size_t>(count, 1024);
         if (r.host)
             cudaFreeHost(r.host);
@@ -1107,13 +1229,13 @@ static gf2x_status take_staging(gf2x_ctx *ctx, size_t count, Staging **out)
         r.host = nullptr;
         r.dev = nullptr;
         r.cap = 0;
-        if (cudaMallocHost((void **)&r.host, cap * sizeof(DevItem)) != cudaSuccess ||
-            cudaMalloc((void **)&r.dev, cap * sizeof(DevItem)) != cudaSuccess)
+        if (ctx_malloc_host(ctx, (void **)&r.host, cap * sizeof(DevItem)) != cudaSuccess ||
+            ctx_malloc(ctx, (void **)&r.dev, cap * sizeof(DevItem)) != cudaSuccess)
             return fail(ctx, GF2X_ENOMEM, "staging allocation");
         r.cap = cap;
     }
-    if (!r.done && cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) != cudaSuccess)
-        return fail(ctx, GF2X_ECUDA, "event creation");
+    if (!r.done)
+        return fail(ctx, GF2X_ECUDA, "staging event missing");
     *out = &r;
     return GF2X_OK;
 }
@@ -1167,6 +1289,15 @@ extern "C" gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, s
         return launch(ctx, args, S, threads, 4ull * smem_words, count, persistent, s);
     }
 
+    if (ctx->fixed && count > kFixedStagingItems) {   // pieces that fit the fixed item staging
+        for (size_t off = 0; off < count; off += kFixedStagingItems) {
+            gf2x_status st = gf2x_mul_batched(ctx, items + off, std::min(kFixedStagingItems, count - off),
+                                              batch_flags, stream);
+            if (st != GF2X_OK)
+                return st;
+        }
+        return GF2X_OK;
+    }
     // resolve plans and check every item
     auto &dv = ctx->scratch_items;
     auto &Ss = ctx->scratch_S;
@@ -1271,6 +1402,24 @@ extern "C" gf2x_status gf2x_ctx_sync_status(gf2x_ctx *ctx, gf2x_stream stream)
         return fail(ctx, GF2X_EDEVICE, buf);
     }
     return GF2X_OK;
+}
+
+extern "C" gf2x_status gf2x_ctx_wait(gf2x_ctx *ctx, gf2x_stream stream, uint32_t timeout_ms)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery((cudaStream_t)stream);
+        if (e == cudaSuccess)
+            break;
+        if (e != cudaErrorNotReady)
+            return cuda_fail(ctx, e, "stream query");
+        if (std::chrono::steady_clock::now() >= deadline)
+            return fail(ctx, GF2X_ETIMEOUT, "the stream's work did not finish within the wait limit");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    return gf2x_ctx_sync_status(ctx, stream);   // complete: the error word and asynchronous errors
 }
 
 extern "C" const char *gf2x_ctx_last_error(gf2x_ctx *ctx)

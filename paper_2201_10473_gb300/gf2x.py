@@ -71,7 +71,10 @@ _SIGNATURES = {
     "gf2x_default_spec": ([_U32, ctypes.POINTER(PlanSpec)], _I),
     "gf2x_plan_info_get": ([_U32, ctypes.POINTER(PlanSpec), ctypes.POINTER(PlanInfo)], _I),
     "gf2x_spec_parse": ([ctypes.c_char_p, ctypes.POINTER(PlanSpec)], _I),
-    "gf2x_ctx_create": ([ctypes.POINTER(_P), _I], _I),
+    "gf2x_ctx_create": ([ctypes.POINTER(_P), _I, _SZ, ctypes.c_char_p], _I),
+    "gf2x_ctx_alloc_count": ([_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], _I),
+    "gf2x_debug_fail_next_allocs": ([_U32], _U32),
+    "gf2x_ctx_wait": ([_P, _P, _U32], _I),
     "gf2x_ctx_destroy": ([_P], None),
     "gf2x_ctx_set_plan": ([_P, _U32, ctypes.POINTER(PlanSpec)], _I),
     "gf2x_ctx_get_plan": ([_P, _U32, ctypes.POINTER(PlanSpec)], _I),
@@ -197,14 +200,17 @@ class Context:
 
     plan_db: a plan database file to install ("packaged" = the GB300-tuned
     database shipped with the package, None = the library's model-based
-    default plans); batch_hint selects its batch bucket."""
+    default plans); batch_hint selects its batch bucket.
+    workspace_bytes: 0 = scratch grows on demand; > 0 = one device arena of
+    that size allocated now, and no compute call allocates afterwards."""
 
-    def __init__(self, device: int | None = None, plan_db: str | None = "packaged", batch_hint: int = 2048):
+    def __init__(self, device: int | None = None, plan_db: str | None = "packaged", batch_hint: int = 2048,
+                 workspace_bytes: int = 0):
         if device is None:
             device = torch.cuda.current_device()
         self.device = device
         h = ctypes.c_void_p()
-        st = lib().gf2x_ctx_create(ctypes.byref(h), device)
+        st = lib().gf2x_ctx_create(ctypes.byref(h), device, workspace_bytes, None)
         if st:
             raise Gf2xError(st, "gf2x_ctx_create")
         self._h = h
@@ -258,6 +264,20 @@ class Context:
 
     def sync_status(self, stream=None):
         self._raise(lib().gf2x_ctx_sync_status(self._h, _stream_handle(stream)), "sync_status")
+
+    def wait(self, timeout_ms: int, stream=None) -> int:
+        """gf2x_ctx_wait: the status code (0, or GF2X_ETIMEOUT = 4 when the
+        stream's work is not done within timeout_ms); other errors raise."""
+        st = lib().gf2x_ctx_wait(self._h, _stream_handle(stream), timeout_ms)
+        if st not in (0, 4):
+            self._raise(st, "wait")
+        return st
+
+    def alloc_count(self) -> tuple[int, int]:
+        """(device + pinned allocations, their bytes) made by this context so far."""
+        n, b = ctypes.c_uint64(), ctypes.c_uint64()
+        self._raise(lib().gf2x_ctx_alloc_count(self._h, ctypes.byref(n), ctypes.byref(b)), "alloc_count")
+        return n.value, b.value
 
     # products
     def mul(self, a: torch.Tensor, b: torch.Tensor, n: int, out: torch.Tensor | None = None, stream=None):
