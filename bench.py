@@ -410,9 +410,20 @@ def run_ours(args, w):
     peak = SMS * ALU_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     traffic = measured_traffic(w["name"], spec)
     observed = clk.get("sm_mhz")
+    # the leaf products' useful AND-XORs alone (one 32-bit AND-XOR per 32 bit
+    # products: the word products of the plan x 64 x 64 / 32), without the
+    # comb's shifts and masks or the evaluation / interpolation passes
+    useful = info["nleaves"] * 32 * info["leaf_words"] ** 2
+    useful_achieved = useful * batch / (mean_launch_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
             "traffic": traffic,
             "ops_per_product": info["ops_full"], "products_per_launch": batch,
+            "useful_leaf_ops_per_product": useful, "useful_leaf_achieved": useful_achieved,
+            "frac_useful_leaf_ops": useful_achieved / peak,
+            "clmul64_per_product": info["clmul64"],
+            # plan-independent context: the schoolbook's n^2 bit products as 32-bit AND-XORs per second
+            # (what the recursion saves shows up as a rate above the peak)
+            "schoolbook_equivalent_tops": (n * n / 32) * batch / (mean_launch_ms * 1e-3) / 1e12,
             "peak_note": "152 SMs x 64 ALU lanes/clk x 2070 MHz (unit counts and max clock)",
             "frac_at_observed_clock": (achieved / (SMS * ALU_LANES_PER_SM * observed * 1e6 / 1e12)) if observed else None,
             "hbm_gbs": (info["bytes_in"] + (info["bytes_out_reduced"] if reduce else info["bytes_out_full"])) * batch

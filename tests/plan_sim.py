@@ -158,3 +158,52 @@ def parse_levels(text: str):
     for tok in filter(None, text.split(".")):
         out.append((tok[0], int(tok[1:])))
     return out
+
+
+# ---------------------------------------------------------------- operation counts
+# A second derivation of the library's modelled operation count (the unit of
+# bench.py's roofline): the comb leaf counted from its loop nest, the
+# Karatsuba and Toom-3 levels counted node by node down the recursion tree
+# (the library multiplies per-level counts by the number of parents).  A
+# change of either side's model makes tests/test_plan_ops.py fail.
+
+def comb_ops(S: int) -> int:
+    """32-bit operations of the S-word comb leaf, counted loop by loop."""
+    ops = 3 * (1 + (S - 1) + 1)              # a X^8, a X^16, a X^24: first shift, S-1 funnel shifts, last shift
+    for _u in range(8):                      # eight steps of one bit per byte
+        ops += (2 * S - 1) + 1               # accumulator shifted left by one: funnel shifts and the low word
+        for _i in range(S):                  # every word of b
+            ops += 4                         # four byte-sign masks
+            ops += 1                         # b word shifted
+            ops += (S + 1) * 3 + S           # AND-XORs of a X^24, a X^16, a X^8 (S+1 words) and a (S words)
+    return ops
+
+
+def karatsuba_node_ops(k: int, E: int) -> int:
+    pairs = [c for c in karatsuba_children(k) if len(c) == 2]
+    ev = sum(2 * E for _ in pairs)           # A and B pair sums, E words each
+    nterms = 0
+    for p in range(2 * k - 1):
+        nterms += sum(1 for i in range(k) if 0 <= p - i < k)
+        nterms += sum(1 for i in range(k) if i < p - i < k)
+    return ev + nterms * 2 * E - 2 * (k * E)  # every term XORed in, less the first writes of the 2T words
+
+
+def toom3_node_ops(W: int, E: int) -> int:
+    npr = E - 2 * W
+    return 2 * (2 * npr + 4 * E) + 36 * npr  # evaluation of A and B; two /x, two /(x+1), recomposition
+
+
+def modelled_ops(levels, S: int, n: int) -> int:
+    """Modelled operations of one full product of size n under the plan."""
+    sz = sizes(levels, S)
+
+    def node(depth):
+        if depth == len(levels):
+            return comb_ops(S)
+        kind, arg = levels[depth]
+        E = sz[depth + 1]
+        if kind == "K":
+            return karatsuba_node_ops(arg, E) + len(karatsuba_children(arg)) * node(depth + 1)
+        return toom3_node_ops(arg, E) + 5 * node(depth + 1)
+    return node(0) + 4 * ((n + 63) // 64)     # the fold and store: two words per output limb, two operations each
