@@ -354,6 +354,34 @@ gf2x_status gf2x_mul_toom4(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, cons
 gf2x_status gf2x_mul_toom5(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b, uint32_t n,
                            size_t count, size_t stride_in, size_t stride_out, uint32_t flags, gf2x_stream stream);
 
+/* Products r_j = a * b_j mod X^n - 1 of ONE polynomial a with `count`
+ * polynomials b_j on the tensor cores: the circulant matrix of a (Sec. 1)
+ * times the matrix of the b_j as an integer GEMM in block-scaled fp4
+ * (tcgen05.mma kind::mxf4, operands 0/1, every scale 1.0, exact fp32 counts
+ * in tensor memory), the product bits being the counts' parities.  For the
+ * operand shape of Sec. 1 where one public polynomial (an HQC/BIKE key)
+ * multiplies many vectors; results equal gf2x_mul_strided with
+ * GF2X_BATCH_SHARED_A and GF2X_REDUCE, bit for bit.
+ *  - a: ceil(n/64) limbs; b: count rows, stride_b limbs apart; r: count
+ *    rows of ceil(n/64) limbs, stride_r limbs apart (bits above n ignored in
+ *    the operands, zero in the results).
+ *  - n odd, 1 <= n <= 65535 (the HQC and BIKE moduli are primes), else
+ *    GF2X_EUNSUPPORTED.  The work is n^2 multiply-adds per product, so the
+ *    call pays at the smaller sizes; the Karatsuba/Toom path wins again as n
+ *    grows.
+ *  - Launches on `stream`: the sequence of a, then per group of products an
+ *    unpacking kernel, the GEMM (persistent, one CTA per SM, all of its
+ *    tensor memory) and a reordering kernel.  Scratch: the context buffer of
+ *    gf2x_mul_unbalanced, about (count/128) ceil(n/64) 4 KiB + count n/8
+ *    bytes plus 8 n bytes for a.  A kernel wait that runs out (none is
+ *    expected) is reported by gf2x_ctx_sync_status as GF2X_ETIMEOUT.
+ *  - Constant time: addresses and branches depend on n and count only.
+ *  - Errors: GF2X_EINVAL for null or misaligned pointers, short strides,
+ *    results overlapping a or b; GF2X_ENOMEM when the scratch cannot hold a
+ *    group of 128 products. */
+gf2x_status gf2x_mulmod_shared_tc(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a, const uint64_t *b, uint32_t n,
+                                  size_t count, size_t stride_b, size_t stride_r, gf2x_stream stream);
+
 /* The kernel shape gf2x_mulmod_sparse uses for n (host only, needs no GPU).
  * The warp's cyclic window is 32 x words_per_lane words; the word offset's
  * bits are applied by shared_stages shifts in shared memory (the largest,

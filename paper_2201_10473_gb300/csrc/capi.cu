@@ -256,6 +256,8 @@ extern "C" gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device, size_t worksp
     if (e == cudaSuccess)
         e = prepare_split();
     if (e == cudaSuccess)
+        e = prepare_tc();
+    if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&ctx->ws_done, cudaEventDisableTiming);
     if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&ctx->ub_done, cudaEventDisableTiming);
@@ -1092,6 +1094,59 @@ extern "C" gf2x_status gf2x_mul_toom5(gf2x_ctx *ctx, uint64_t *out, const uint64
     return run_toom(ctx, 5u, out, a, b, n, count, stride_in, stride_out, flags, stream);
 }
 
+extern "C" gf2x_status gf2x_mulmod_shared_tc(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a, const uint64_t *b,
+                                             uint32_t n, size_t count, size_t stride_b, size_t stride_r,
+                                             gf2x_stream stream)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    if (count == 0)
+        return GF2X_OK;
+    if (n < 1 || n > kTcMaxN || !(n & 1u))
+        return fail(ctx, GF2X_EUNSUPPORTED, "tensor-core circulant products need an odd n in [1, 65535]");
+    if (!r || !a || !b)
+        return fail(ctx, GF2X_EINVAL, "null operand or result pointer");
+    if (((uintptr_t)r | (uintptr_t)a | (uintptr_t)b) & 7u)
+        return fail(ctx, GF2X_EINVAL, "operands and results must be 8-byte aligned");
+    const size_t L = (n + 63) / 64;
+    if (count > 1 && (stride_b < L || stride_r < L))
+        return fail(ctx, GF2X_EINVAL, "stride smaller than the operand or result size");
+    if (count > 0x7fffffffull)
+        return fail(ctx, GF2X_EINVAL, "batch too large");
+    const size_t r_bytes = 8 * ((count - 1) * stride_r + L);
+    if (ranges_overlap(r, r_bytes, a, 8 * L) || ranges_overlap(r, r_bytes, b, 8 * ((count - 1) * stride_b + L)))
+        return fail(ctx, GF2X_EINVAL, "result overlaps an operand");
+    TcShape sh;
+    if (!tc_shape(n, count, &sh))
+        return fail(ctx, GF2X_EUNSUPPORTED, "no tensor-core shape for this n");
+    // scratch: R, then per group of products (a multiple of 128) the fp4
+    // chunks of b and the parities in position-index order
+    const size_t rbytes = (sh.rseq_bytes + 255) / 256 * 256;
+    const size_t cap = scratch_cap(ctx);
+    size_t group = (count + 127) / 128 * 128;
+    while (group > 128 && rbytes + tc_group_bytes(sh, group) > cap)
+        group = (group / 2 + 127) / 128 * 128;
+    const size_t want = rbytes + tc_group_bytes(sh, std::min(group, count));
+    if (want > cap)
+        return fail(ctx, GF2X_ENOMEM, "scratch too small for one tile of 128 products");
+    cudaStream_t s = (cudaStream_t)stream;
+    gf2x_status st = scratch_acquire(ctx, want, s);
+    if (st != GF2X_OK)
+        return st;
+    uint8_t *base = reinterpret_cast<uint8_t *>(ctx->ub);
+    cudaError_t e = launch_tc_rseq(a, n, sh, base, ctx->sm_count, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "tensor-core sequence launch");
+    for (size_t c0 = 0; c0 < count; c0 += group) {
+        const size_t g = std::min(group, count - c0);
+        e = launch_tc_group(b + c0 * stride_b, stride_b, r + c0 * stride_r, stride_r, n, (uint32_t)g, sh, base,
+                            base + rbytes, ctx->err_dev, ctx->sm_count, s);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "tensor-core product launch");
+    }
+    return scratch_release(ctx, s);
+}
+
 // k rows of `width` limbs, `dpitch` / `spitch` limbs apart.
 static cudaError_t copy_rows(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, size_t k,
                              cudaMemcpyKind kind, cudaStream_t st)
@@ -1398,6 +1453,10 @@ extern "C" gf2x_status gf2x_ctx_sync_status(gf2x_ctx *ctx, gf2x_stream stream)
     if (flags) {
         cudaMemset(ctx->err_dev, 0, sizeof(uint32_t));
         char buf[128];
+        if (flags & kErrTimeout) {
+            snprintf(buf, sizeof(buf), "a bounded wait in a kernel ran out (flags 0x%x)", flags);
+            return fail(ctx, GF2X_ETIMEOUT, buf);
+        }
         snprintf(buf, sizeof(buf), "checked kernel reported invariant violation flags 0x%x", flags);
         return fail(ctx, GF2X_EDEVICE, buf);
     }

@@ -65,6 +65,25 @@ size_t toom_interp_smem(uint32_t K, const ToomArgs &a);
 cudaError_t launch_toom_eval(uint32_t K, const ToomArgs &a, unsigned grid, cudaStream_t st);
 cudaError_t launch_toom_interp(uint32_t K, const ToomArgs &a, unsigned grid, cudaStream_t st);
 
+// shared-operand circulant products on the tensor cores (tc_circulant.cu)
+constexpr uint32_t kTcMaxN = 65536;
+struct TcShape {
+    uint32_t S;               // K-steps of 64 inputs (limbs of b)
+    uint32_t V;               // units of 480 positions
+    uint32_t qwords;          // 32-bit words of parities per product (q order)
+    uint32_t rwin;            // bytes of one unit's window of R
+    uint32_t inv32;           // 32^-1 mod n
+    size_t rseq_bytes;        // bytes of R
+};
+bool tc_shape(uint32_t n, size_t count, TcShape *sh);   // n odd, 1 <= n <= kTcMaxN
+size_t tc_group_bytes(const TcShape &sh, size_t products);
+cudaError_t prepare_tc();
+cudaError_t launch_tc_rseq(const uint64_t *a, uint32_t n, const TcShape &sh, uint8_t *rseq, int sm_count,
+                           cudaStream_t st);
+cudaError_t launch_tc_group(const uint64_t *b, size_t stride_b, uint64_t *out, size_t stride_out, uint32_t n,
+                            uint32_t count, const TcShape &sh, const uint8_t *rseq, uint8_t *scratch, uint32_t *err,
+                            int sm_count, cudaStream_t st);
+
 typedef cudaError_t (*LaunchFn)(const LaunchArgs &, unsigned, unsigned, size_t, cudaStream_t);
 typedef cudaError_t (*PrepareFn)(int *, unsigned, size_t);
 

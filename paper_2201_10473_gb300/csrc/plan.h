@@ -103,6 +103,7 @@ constexpr uint32_t kNoPlan = 0xffffffffu;
 constexpr uint32_t kEmptyItem = 0xfffffffeu;  // device item with n = 0: a padding slot, skipped
 
 // Checked-mode error codes (bit flags, OR-ed into *err).
-enum : uint32_t { kErrDivX = 1, kErrDivX1 = 2, kErrPad = 4, kErrNoPlan = 8, kErrPlanMismatch = 16, kErrDivX2X1 = 32 };
+enum : uint32_t { kErrDivX = 1, kErrDivX1 = 2, kErrPad = 4, kErrNoPlan = 8, kErrPlanMismatch = 16, kErrDivX2X1 = 32,
+                 kErrTimeout = 64 };   // kErrTimeout: a bounded wait in a kernel ran out
 
 }  // namespace gf2x

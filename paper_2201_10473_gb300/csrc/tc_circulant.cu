@@ -1,0 +1,524 @@
+// tc_circulant.cu -- r_j = a * b_j mod (X^n - 1) for ONE polynomial a and
+// many b_j (the shared-operand batch: an HQC/BIKE public key times many
+// vectors, Sec. 1) as an integer GEMM on the fifth-generation tensor cores.
+//
+// Sec. 1 maps the product in F2[X]/(X^n - 1) to the circulant matrix of a
+// times the vector b: r[p] = sum_k a[(p - k) mod n] b[k] over F2.  With one a
+// for the whole batch this is D = B * T with B = [b_j] (count x n, 0/1) and
+// T[k][p] = a[(p - k) mod n], and r_j[p] = D[j][p] mod 2.  The GEMM runs in
+// block-scaled fp4 (tcgen05.mma kind::mxf4, every scale factor 1.0): the
+// operands are the bits as e2m1 0.0 / 1.0 (nibble 0 / 2), the counts
+// accumulate exactly in fp32 TMEM (at most n < 2^24), and the product bit
+// is the count's parity.
+//
+// The circulant operand costs nothing per MMA.  Its row for output position
+// p is a reversed window of a, and the rows of one MMA are the positions
+// p0, p0 - 32, p0 - 64, ... (mod n): row q then starts exactly 16 bytes (32
+// fp4 elements) after row q - 1 in ONE nibble sequence R[t] = a[(p0 - t) mod
+// n], so a shared-memory descriptor with a 16-byte leading and a 128-byte
+// stride offset reads the whole 240 x 64 operand tile out of R.  For odd n
+// the stride -32 mod n visits every position once, so the positions are
+// enumerated as q = 0, 1, 2, ... with p(q) = (n - 1 - 32 q) mod n.
+//
+// Kernels (all on the caller's stream):
+//  tc_rseq_kernel     R, the nibble sequence of a (once per call);
+//  tc_unpack_kernel   the b rows as fp4 nibbles in the UMMA K-major layout,
+//                     one 4 KB chunk per tile of 128 rows and K-step of 64;
+//  tc_gemm_kernel     persistent, one CTA per SM: a bulk-copy producer
+//                     thread, an MMA thread, four epilogue warps reading the
+//                     counts from TMEM; each unit is 128 products x 480
+//                     positions over all n inputs; the parities go out in
+//                     position-index (q) order;
+//  tc_assemble_kernel q order -> bit order: r_j[p] = parity[j][q(p)], a
+//                     funnel-shift gather of each bit column and a warp
+//                     ballot transpose per 32 output words.
+// Constant time: every loop bound, address and branch depends on n, count
+// and thread indices only; operand bits flow through data paths.
+// Every wait on a barrier is bounded (globaltimer); on a timeout the CTA
+// records kErrTimeout, drains its copies and MMAs (bounded) and frees TMEM.
+#include <algorithm>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "gf2x_gb300.h"
+#include "launchers.h"
+
+namespace gf2x {
+
+namespace {
+
+constexpr uint32_t kTcThreads = 256;          // warps: 0 producer, 1 MMA, 2-3 idle, 4-7 epilogue
+constexpr uint32_t kRing = 16;                // A stages
+constexpr uint32_t kChunk = 4096;             // bytes of one A stage: 128 rows x 64 fp4
+constexpr uint32_t kNT = 240;                 // N of one MMA
+constexpr uint32_t kNU = 2 * kNT;             // positions per unit
+constexpr uint32_t kSfCol = kNU;              // TMEM columns kNU..511 hold the scale factors (all 1.0)
+constexpr uint32_t kRWinMax = 16 * (kNU - 1) + 32 * (kTcMaxN / 64);   // bytes of an R window
+constexpr uint32_t kROff = kRing * kChunk;
+constexpr uint32_t kRBytes = (kRWinMax + 127) / 128 * 128;
+constexpr uint32_t kBarOff = kROff + 2 * kRBytes;
+constexpr uint32_t kSmemBytes = kBarOff + 512;   // > 114 KB: one CTA per SM (the whole TMEM)
+constexpr uint64_t kWaitLimitNs = 2000000000ull; // 2 s per wait
+
+// e2m1 1.0 = 0b0010; element 2i in the low nibble of byte i
+__device__ __forceinline__ uint32_t spread8(uint32_t x)
+{
+    uint32_t t = x & 0xffu;
+    t = (t | (t << 12)) & 0x000f000fu;
+    t = (t | (t << 6)) & 0x03030303u;
+    t = (t | (t << 3)) & 0x11111111u;
+    return t << 1;
+}
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtime()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// UMMA shared-memory descriptor, no swizzle: start, leading (K) byte offset,
+// stride (M/N, 8-row group) byte offset, descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3ffffu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::mxf4 instruction descriptor: A and B e2m1 (1), K-major, N, M = 128,
+// scale factors ue8m0 (bit 23), scale-factor ids 0.
+constexpr uint32_t kIdesc = (1u << 7) | (1u << 10) | ((kNT >> 3) << 17) | (1u << 23) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on a barrier phase; false on a timeout or when another role
+// has aborted (the shared abort word).
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t *abort_flag)
+{
+    const uint64_t t0 = gtime();
+    for (;;) {
+        if (mbar_test(bar, parity))
+            return true;
+        if (*abort_flag)
+            return false;
+        if (gtime() - t0 > kWaitLimitNs)
+            return false;
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_fp4(uint32_t d, uint64_t a, uint64_t b, uint32_t sfa, uint32_t sfb, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%5], [%6], p;\n}"
+                 ::"r"(d), "l"(a), "l"(b), "r"(kIdesc), "r"(acc), "r"(sfa), "r"(sfb));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+}  // namespace
+
+// R[t] = a[(n - 1 - t) mod n] as fp4 nibbles, `words` 32-bit words of 8.
+__global__ void __launch_bounds__(256) tc_rseq_kernel(const uint64_t *__restrict__ a, uint32_t n,
+                                                      uint32_t *__restrict__ r, uint32_t words)
+{
+    const uint32_t top = n - 1;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < words; w += gridDim.x * blockDim.x) {
+        uint32_t bits = 0;
+        uint32_t i = (uint32_t)((top + (uint64_t)n - (8ull * w) % n) % n);   // (n-1-8w) mod n
+#pragma unroll
+        for (uint32_t e = 0; e < 8; ++e) {
+            bits |= (uint32_t)((a[i >> 6] >> (i & 63u)) & 1u) << e;
+            i = i == 0 ? top : i - 1;     // the index only, never the bit, decides
+        }
+        r[w] = spread8(bits);
+    }
+}
+
+// b rows -> A chunks: chunk (tile, s) holds rows tile*128 .. +127, inputs
+// 64 s .. 64 s + 63, core matrix (row group g, K half c) at g*256 + c*128,
+// row r of it at + 16 r.  Rows past `count` and bits past n are zero.
+__global__ void __launch_bounds__(256) tc_unpack_kernel(const uint64_t *__restrict__ b, size_t stride_b, uint32_t n,
+                                                        uint32_t count, uint32_t S, uint32_t tiles,
+                                                        uint8_t *__restrict__ chunks)
+{
+    const uint32_t L = (n + 63) / 64;
+    const uint64_t top = (n & 63u) ? ((1ull << (n & 63u)) - 1ull) : ~0ull;
+    const uint64_t total = (uint64_t)tiles * S * 128u;
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = (uint32_t)(idx & 127u);
+        const uint64_t ts = idx >> 7;
+        const uint32_t s = (uint32_t)(ts % S), tile = (uint32_t)(ts / S);
+        const uint32_t row = tile * 128u + j;
+        uint64_t v = 0;
+        if (row < count && s < L) {
+            v = b[(size_t)row * stride_b + s];
+            if (s == L - 1)
+                v &= top;
+        }
+        const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+        uint4 q0, q1;
+        q0.x = spread8(lo);
+        q0.y = spread8(lo >> 8);
+        q0.z = spread8(lo >> 16);
+        q0.w = spread8(lo >> 24);
+        q1.x = spread8(hi);
+        q1.y = spread8(hi >> 8);
+        q1.z = spread8(hi >> 16);
+        q1.w = spread8(hi >> 24);
+        uint8_t *base = chunks + ((uint64_t)tile * S + s) * kChunk + (j >> 3) * 256u + (j & 7u) * 16u;
+        *reinterpret_cast<uint4 *>(base) = q0;
+        *reinterpret_cast<uint4 *>(base + 128) = q1;
+    }
+}
+
+struct TcGemmArgs {
+    const uint8_t *chunks;    // A chunks (tc_unpack_kernel)
+    const uint8_t *rseq;      // R (tc_rseq_kernel), 16-byte aligned
+    uint32_t *qbits;          // per product qwords 32-bit words of parities in q order
+    uint32_t *err;            // error word (kErrTimeout), may be null
+    uint32_t S;               // K-steps (limbs of b)
+    uint32_t V;               // position units per product tile
+    uint32_t units;           // tiles x V
+    uint32_t count;
+    uint32_t qwords;          // V * kNU / 32
+    uint32_t rwin;            // bytes of one unit's R window
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const TcGemmArgs args)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t sbase = su32(sm);
+    // barriers: full[kRing], empty[kRing], rfull[2], rempty[2], done, tfree
+    const uint32_t bar0 = sbase + kBarOff;
+    auto full = [&](uint32_t i) { return bar0 + 8u * i; };
+    auto empty = [&](uint32_t i) { return bar0 + 8u * (kRing + i); };
+    auto rfull = [&](uint32_t i) { return bar0 + 8u * (2 * kRing + i); };
+    auto rempty = [&](uint32_t i) { return bar0 + 8u * (2 * kRing + 2 + i); };
+    const uint32_t done = bar0 + 8u * (2 * kRing + 4), tfree = bar0 + 8u * (2 * kRing + 5);
+    const uint32_t drain = bar0 + 8u * (2 * kRing + 6);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kBarOff + 8u * (2 * kRing + 8));
+    volatile uint32_t *abort_flag = tslot + 1;
+
+    if (threadIdx.x == 0) {
+        for (uint32_t i = 0; i < kRing; ++i) {
+            mbar_init(full(i), 1);
+            mbar_init(empty(i), 1);
+        }
+        for (uint32_t i = 0; i < 2; ++i) {
+            mbar_init(rfull(i), 1);
+            mbar_init(rempty(i), 1);
+        }
+        mbar_init(done, 1);
+        mbar_init(tfree, 4);   // one arrival per epilogue warp
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    if (warp >= 4) {   // scale factors: every byte 0x7F (ue8m0 1.0) in columns kSfCol..511
+        const uint32_t v = 0x7f7f7f7fu;
+        for (uint32_t c = kSfCol; c < 512u; c += 8)
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};"
+                         ::"r"(tmem + (((warp & 3u) * 32u) << 16) + c), "r"(v));
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+
+    const uint32_t S = args.S;
+    bool failed = false;
+    if (warp == 0 && lane == 0) {
+        // ---- producer: R window per unit (two buffers), A chunks through the ring
+        uint32_t g = 0, k = 0;
+        for (uint32_t u = blockIdx.x; u < args.units && !failed; u += gridDim.x, ++k) {
+            const uint32_t tile = u / args.V, v = u - tile * args.V;
+            const uint32_t rb = k & 1u;
+            if (k >= 2 && !mbar_wait(rempty(rb), ((k >> 1) - 1u) & 1u, abort_flag)) {
+                failed = true;
+                break;
+            }
+            bulk_load(sbase + kROff + rb * kRBytes, args.rseq + (size_t)v * (16u * kNU), args.rwin, rfull(rb));
+            const uint8_t *src = args.chunks + (size_t)tile * S * kChunk;
+            for (uint32_t s = 0; s < S; ++s, ++g) {
+                const uint32_t slot = g % kRing;
+                if (g >= kRing && !mbar_wait(empty(slot), ((g / kRing) - 1u) & 1u, abort_flag)) {
+                    failed = true;
+                    break;
+                }
+                bulk_load(sbase + slot * kChunk, src + (size_t)s * kChunk, kChunk, full(slot));
+            }
+        }
+        if (failed) {   // let the copies already issued land before the CTA can exit
+            *abort_flag = 1;
+            const uint64_t t0 = gtime();
+            for (uint32_t h = (g > kRing ? g - kRing : 0); h < g; ++h)
+                while (!mbar_test(full(h % kRing), (h / kRing) & 1u) && gtime() - t0 < 100000000ull) {
+                }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        uint32_t g = 0, k = 0;
+        bool issued = false;
+        for (uint32_t u = blockIdx.x; u < args.units && !failed; u += gridDim.x, ++k) {
+            const uint32_t rb = k & 1u;
+            if (!mbar_wait(rfull(rb), (k >> 1) & 1u, abort_flag) ||
+                (k >= 1 && !mbar_wait(tfree, (k - 1u) & 1u, abort_flag))) {
+                failed = true;
+                break;
+            }
+            fence_after();
+            const uint32_t rwin = sbase + kROff + rb * kRBytes;
+            for (uint32_t s = 0; s < S; ++s, ++g) {
+                const uint32_t slot = g % kRing;
+                if (!mbar_wait(full(slot), (g / kRing) & 1u, abort_flag)) {
+                    failed = true;
+                    break;
+                }
+                fence_after();
+                const uint64_t adesc = sdesc(sbase + slot * kChunk, 128, 256);
+                mma_fp4(tmem, adesc, sdesc(rwin + 32u * s, 16, 128), tmem + kSfCol, tmem + kSfCol + 16, s > 0);
+                mma_fp4(tmem + kNT, adesc, sdesc(rwin + 16u * kNT + 32u * s, 16, 128), tmem + kSfCol,
+                        tmem + kSfCol + 16, s > 0);
+                issued = true;
+                mma_commit(empty(slot));   // the stage is free once these MMAs have read it
+            }
+            if (failed)
+                break;
+            mma_commit(rempty(rb));
+            mma_commit(done);
+        }
+        if (failed) {
+            *abort_flag = 1;
+            if (issued) {   // wait (bounded) for the MMAs in flight before TMEM is freed
+                mma_commit(drain);
+                const uint64_t t0 = gtime();
+                while (!mbar_test(drain, 0) && gtime() - t0 < 100000000ull) {
+                }
+            }
+        }
+    } else if (warp >= 4) {
+        // ---- epilogue: counts -> parities, 480 positions of 32 products per warp
+        const uint32_t wq = warp & 3u;
+        uint32_t k = 0;
+        for (uint32_t u = blockIdx.x; u < args.units; u += gridDim.x, ++k) {
+            const uint32_t tile = u / args.V, v = u - tile * args.V;
+            const bool ok = mbar_wait(done, k & 1u, abort_flag);
+            if (!__all_sync(0xffffffffu, ok)) {   // warp-uniform: the loads below are warp-synchronous
+                failed = true;
+                break;
+            }
+            fence_after();
+            const uint32_t row = tile * 128u + wq * 32u + lane;
+            uint32_t *dst = args.qbits + (size_t)row * args.qwords + (size_t)v * (kNU / 32u);
+#pragma unroll 1
+            for (uint32_t c = 0; c < kNU; c += 32) {
+                uint32_t r[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(tmem + ((wq * 32u) << 16) + c));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                uint32_t word = 0;
+#pragma unroll
+                for (uint32_t i = 0; i < 32; ++i)   // exact integer count c < 2^23: bit 0 of 2^23 + c is its parity
+                    word |= (__float_as_uint(__uint_as_float(r[i]) + 8388608.0f) & 1u) << i;
+                if (row < args.count)
+                    dst[c / 32u] = word;
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(tfree);
+        }
+        if (failed)
+            *abort_flag = 1;
+    }
+    __syncwarp();
+    if (failed && args.err && lane == 0)
+        atomicOr(args.err, kErrTimeout);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// r_j in bit order from the parities in q order: for output words w0 .. w0+31
+// and bit e, q(32 w + e) = (Q_e - w) mod n with Q_e = (n - 1 - e) inv32 mod n,
+// a run of 32 q's read backwards; lane e gathers it (funnel shift, or bit by
+// bit where it wraps past q = 0), the warp transposes by ballots.
+__global__ void __launch_bounds__(256) tc_assemble_kernel(const uint32_t *__restrict__ qbits, uint32_t qwords,
+                                                          uint32_t n, uint32_t inv32, uint32_t count,
+                                                          uint64_t *__restrict__ out, size_t stride_out)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t L32 = (n + 31) / 32, blocks = (L32 + 31) / 32;
+    const uint64_t tasks = (uint64_t)count * blocks;
+    const uint32_t Qe = (uint32_t)(((uint64_t)(n - 1u - (lane % n)) % n * inv32) % n);
+    for (uint64_t t = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); t < tasks;
+         t += (uint64_t)gridDim.x * (blockDim.x / 32)) {
+        const uint32_t j = (uint32_t)(t / blocks), blk = (uint32_t)(t - (uint64_t)j * blocks);
+        const uint32_t w0 = blk * 32u;
+        const uint32_t *row = qbits + (size_t)j * qwords;
+        // q run: start = (Q_e - w0 - 31) mod n, 32 bits
+        const uint32_t start = (uint32_t)(((uint64_t)Qe + 32ull * n - (w0 % n) - 31u) % n);
+        uint32_t x;
+        if (start + 31u < n) {
+            const uint32_t lo = row[start >> 5], hi = row[(start >> 5) + 1u];
+            x = __funnelshift_r(lo, hi, start & 31u);
+        } else {   // the run wraps past q = n - 1 (sizes only decide this)
+            x = 0;
+            uint32_t q = start;
+            for (uint32_t i = 0; i < 32u; ++i) {
+                x |= ((row[q >> 5] >> (q & 31u)) & 1u) << i;
+                q = q + 1u == n ? 0u : q + 1u;
+            }
+        }
+        x = __brev(x);   // bit i <-> word w0 + i
+        uint32_t mine = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < 32u; ++i) {
+            const uint32_t col = __ballot_sync(0xffffffffu, (x >> i) & 1u);   // word w0 + i, bit e from lane e
+            if (lane == i)
+                mine = col;
+        }
+        const uint32_t w = w0 + lane;
+        if (w < L32) {
+            if (w == L32 - 1u && (n & 31u))
+                mine &= (1u << (n & 31u)) - 1u;
+            reinterpret_cast<uint32_t *>(out + (size_t)j * stride_out)[w] = mine;
+        } else if (w < 2u * ((n + 63u) / 64u)) {
+            reinterpret_cast<uint32_t *>(out + (size_t)j * stride_out)[w] = 0u;   // the top limb's upper half
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+bool tc_shape(uint32_t n, size_t count, TcShape *sh)
+{
+    if (n < 1 || n > kTcMaxN || !(n & 1u) || count == 0)
+        return false;
+    sh->S = (n + 63) / 64;
+    sh->V = (n + kNU - 1) / kNU;
+    sh->qwords = sh->V * (kNU / 32u);
+    sh->rwin = 16u * (kNU - 1u) + 32u * sh->S;               // bytes of one unit's R window (multiple of 16)
+    sh->rseq_bytes = (size_t)16u * kNU * (sh->V - 1u) + sh->rwin;
+    // inverse of 32 mod n (n odd): extended Euclid
+    int64_t t0 = 0, t1 = 1, r0 = n, r1 = 32 % n;
+    while (r1) {
+        const int64_t q = r0 / r1, r2 = r0 - q * r1, t2 = t0 - q * t1;
+        r0 = r1;
+        r1 = r2;
+        t0 = t1;
+        t1 = t2;
+    }
+    sh->inv32 = n == 1 ? 0u : (uint32_t)((t0 % (int64_t)n + n) % n);
+    return true;
+}
+
+size_t tc_group_bytes(const TcShape &sh, size_t products)
+{
+    const size_t tiles = (products + 127) / 128;
+    return tiles * sh.S * (size_t)kChunk + (products * sh.qwords + 2) * 4ull;
+}
+
+cudaError_t prepare_tc()
+{
+    return cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+}
+
+cudaError_t launch_tc_rseq(const uint64_t *a, uint32_t n, const TcShape &sh, uint8_t *rseq, int sm_count,
+                           cudaStream_t st)
+{
+    const uint32_t words = (uint32_t)((sh.rseq_bytes + 3) / 4);
+    tc_rseq_kernel<<<(unsigned)std::min<uint32_t>(4u * sm_count, (words + 255) / 256), 256, 0, st>>>(
+        a, n, reinterpret_cast<uint32_t *>(rseq), words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_group(const uint64_t *b, size_t stride_b, uint64_t *out, size_t stride_out, uint32_t n,
+                            uint32_t count, const TcShape &sh, const uint8_t *rseq, uint8_t *scratch, uint32_t *err,
+                            int sm_count, cudaStream_t st)
+{
+    const uint32_t tiles = (count + 127) / 128;
+    uint8_t *chunks = scratch;
+    uint32_t *qbits = reinterpret_cast<uint32_t *>(scratch + (size_t)tiles * sh.S * kChunk);
+    const uint64_t threads = (uint64_t)tiles * sh.S * 128u;
+    tc_unpack_kernel<<<(unsigned)std::min<uint64_t>(8ull * sm_count, (threads + 255) / 256), 256, 0, st>>>(
+        b, stride_b, n, count, sh.S, tiles, chunks);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    TcGemmArgs g;
+    g.chunks = chunks;
+    g.rseq = rseq;
+    g.qbits = qbits;
+    g.err = err;
+    g.S = sh.S;
+    g.V = sh.V;
+    g.units = tiles * sh.V;
+    g.count = count;
+    g.qwords = sh.qwords;
+    g.rwin = sh.rwin;
+    tc_gemm_kernel<<<std::min<uint32_t>(g.units, (uint32_t)sm_count), kTcThreads, kSmemBytes, st>>>(g);
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    const uint64_t tasks = (uint64_t)count * (((n + 31) / 32 + 31) / 32);
+    tc_assemble_kernel<<<(unsigned)std::min<uint64_t>(8ull * sm_count, (tasks + 7) / 8), 256, 0, st>>>(
+        qbits, sh.qwords, n, sh.inv32, count, out, stride_out);
+    return cudaGetLastError();
+}
+
+}  // namespace gf2x

@@ -86,6 +86,7 @@ _SIGNATURES = {
     "gf2x_mul_unbalanced": ([_P, _P, _P, _U32, _SZ, _P, _U32, _SZ, _SZ, _SZ, _P], _I),
     "gf2x_mulmod_sparse": ([_P, _P, _P, _P, _U32, _U32, _SZ, _SZ, _SZ, _SZ, _P], _I),
     "gf2x_sparse_info_get": ([_U32, _P], _I),
+    "gf2x_mulmod_shared_tc": ([_P, _P, _P, _P, _U32, _SZ, _SZ, _SZ, _P], _I),
     "gf2x_mul_toom4": ([_P, _P, _P, _P, _U32, _SZ, _SZ, _SZ, _U32, _P], _I),
     "gf2x_mul_toom5": ([_P, _P, _P, _P, _U32, _SZ, _SZ, _SZ, _U32, _P], _I),
     "gf2x_mul_batched": ([_P, _P, _SZ, _U32, _P], _I),
@@ -343,6 +344,24 @@ class Context:
         self._raise(lib().gf2x_mul_unbalanced(self._h, O.data_ptr(), A.data_ptr(), na, A.shape[1], B.data_ptr(), nb,
                                               B.shape[1], count, O.shape[1], _stream_handle(stream)),
                     "gf2x_mul_unbalanced")
+        return out
+
+    def mulmod_shared_tc(self, a: torch.Tensor, b: torch.Tensor, n: int, out: torch.Tensor | None = None,
+                         stream=None):
+        """Row p of the result is a * b[p] mod X^n - 1 for ONE a (1-D), on the
+        tensor cores (gf2x_mulmod_shared_tc; n odd, <= 65535)."""
+        if a.dim() != 1 or b.dim() != 2:
+            raise ValueError("a must be 1-D (one polynomial) and b 2-D (one row per product)")
+        _check_operand(a, n, "a")
+        _check_operand(b, n, "b")
+        count = b.shape[0]
+        if out is None:
+            out = torch.empty((count, limbs(n)), dtype=torch.int64, device=b.device)
+        if out.dim() != 2 or out.shape[0] != count or out.shape[1] < limbs(n) or not out.is_contiguous():
+            raise ValueError("bad output tensor")
+        self._raise(lib().gf2x_mulmod_shared_tc(self._h, out.data_ptr(), a.data_ptr(), b.data_ptr(), n, count,
+                                                b.shape[1], out.shape[1], _stream_handle(stream)),
+                    "gf2x_mulmod_shared_tc")
         return out
 
     def mul_toom4(self, a: torch.Tensor, b: torch.Tensor, n: int, reduce: bool, out: torch.Tensor | None = None,
