@@ -49,13 +49,15 @@ namespace gf2x {
 namespace {
 
 constexpr uint32_t kTcThreads = 256;          // warps: 0 producer, 1 MMA, 2-3 idle, 4-7 epilogue
-constexpr uint32_t kRing = 16;                // A stages
-constexpr uint32_t kChunk = 4096;             // bytes of one A stage: 128 rows x 64 fp4
+constexpr uint32_t kKS = 4;                   // K-steps (of 64 inputs) per ring stage
+constexpr uint32_t kRing = 8;                 // A stages
+constexpr uint32_t kChunk = 4096;             // bytes of one K-step of A: 128 rows x 64 fp4
+constexpr uint32_t kStage = kKS * kChunk;
 constexpr uint32_t kNT = 240;                 // N of one MMA
 constexpr uint32_t kNU = 2 * kNT;             // positions per unit
 constexpr uint32_t kSfCol = kNU;              // TMEM columns kNU..511 hold the scale factors (all 1.0)
 constexpr uint32_t kRWinMax = 16 * (kNU - 1) + 32 * (kTcMaxN / 64);   // bytes of an R window
-constexpr uint32_t kROff = kRing * kChunk;
+constexpr uint32_t kROff = kRing * kStage;
 constexpr uint32_t kRBytes = (kRWinMax + 127) / 128 * 128;
 constexpr uint32_t kBarOff = kROff + 2 * kRBytes;
 constexpr uint32_t kSmemBytes = kBarOff + 512;   // > 114 KB: one CTA per SM (the whole TMEM)
@@ -108,9 +110,14 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
 }
 
 // Bounded wait on a barrier phase; false on a timeout or when another role
-// has aborted (the shared abort word).
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t *abort_flag)
+// has aborted (the shared abort word).  The clock is read only once the
+// first test has failed; `nap` > 0 sleeps between tests (threads that wait
+// long and have nothing else to issue).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t *abort_flag,
+                                          uint32_t nap = 0)
 {
+    if (mbar_test(bar, parity))
+        return true;
     const uint64_t t0 = gtime();
     for (;;) {
         if (mbar_test(bar, parity))
@@ -119,6 +126,8 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t *abor
             return false;
         if (gtime() - t0 > kWaitLimitNs)
             return false;
+        if (nap)
+            __nanosleep(nap);
     }
 }
 
@@ -284,13 +293,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const TcGemmArgs
             }
             bulk_load(sbase + kROff + rb * kRBytes, args.rseq + (size_t)v * (16u * kNU), args.rwin, rfull(rb));
             const uint8_t *src = args.chunks + (size_t)tile * S * kChunk;
-            for (uint32_t s = 0; s < S; ++s, ++g) {
-                const uint32_t slot = g % kRing;
+            for (uint32_t s0 = 0; s0 < S; s0 += kKS, ++g) {   // one stage: up to kKS consecutive K-steps
+                const uint32_t slot = g % kRing, ks = min(kKS, S - s0);
                 if (g >= kRing && !mbar_wait(empty(slot), ((g / kRing) - 1u) & 1u, abort_flag)) {
                     failed = true;
                     break;
                 }
-                bulk_load(sbase + slot * kChunk, src + (size_t)s * kChunk, kChunk, full(slot));
+                bulk_load(sbase + slot * kStage, src + (size_t)s0 * kChunk, ks * kChunk, full(slot));
             }
         }
         if (failed) {   // let the copies already issued land before the CTA can exit
@@ -313,17 +322,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const TcGemmArgs
             }
             fence_after();
             const uint32_t rwin = sbase + kROff + rb * kRBytes;
-            for (uint32_t s = 0; s < S; ++s, ++g) {
-                const uint32_t slot = g % kRing;
+            for (uint32_t s0 = 0; s0 < S; s0 += kKS, ++g) {
+                const uint32_t slot = g % kRing, ks = min(kKS, S - s0);
                 if (!mbar_wait(full(slot), (g / kRing) & 1u, abort_flag)) {
                     failed = true;
                     break;
                 }
                 fence_after();
-                const uint64_t adesc = sdesc(sbase + slot * kChunk, 128, 256);
-                mma_fp4(tmem, adesc, sdesc(rwin + 32u * s, 16, 128), tmem + kSfCol, tmem + kSfCol + 16, s > 0);
-                mma_fp4(tmem + kNT, adesc, sdesc(rwin + 16u * kNT + 32u * s, 16, 128), tmem + kSfCol,
-                        tmem + kSfCol + 16, s > 0);
+                for (uint32_t i = 0; i < ks; ++i) {
+                    const uint32_t s = s0 + i;
+                    const uint64_t adesc = sdesc(sbase + slot * kStage + i * kChunk, 128, 256);
+                    mma_fp4(tmem, adesc, sdesc(rwin + 32u * s, 16, 128), tmem + kSfCol, tmem + kSfCol + 16, s > 0);
+                    mma_fp4(tmem + kNT, adesc, sdesc(rwin + 16u * kNT + 32u * s, 16, 128), tmem + kSfCol,
+                            tmem + kSfCol + 16, s > 0);
+                }
                 issued = true;
                 mma_commit(empty(slot));   // the stage is free once these MMAs have read it
             }
@@ -347,7 +359,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const TcGemmArgs
         uint32_t k = 0;
         for (uint32_t u = blockIdx.x; u < args.units; u += gridDim.x, ++k) {
             const uint32_t tile = u / args.V, v = u - tile * args.V;
-            const bool ok = mbar_wait(done, k & 1u, abort_flag);
+            const bool ok = mbar_wait(done, k & 1u, abort_flag, 256);
             if (!__all_sync(0xffffffffu, ok)) {   // warp-uniform: the loads below are warp-synchronous
                 failed = true;
                 break;
@@ -403,15 +415,24 @@ __global__ void __launch_bounds__(256) tc_assemble_kernel(const uint32_t *__rest
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t L32 = (n + 31) / 32, blocks = (L32 + 31) / 32;
-    const uint64_t tasks = (uint64_t)count * blocks;
     const uint32_t Qe = (uint32_t)(((uint64_t)(n - 1u - (lane % n)) % n * inv32) % n);
-    for (uint64_t t = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); t < tasks;
-         t += (uint64_t)gridDim.x * (blockDim.x / 32)) {
-        const uint32_t j = (uint32_t)(t / blocks), blk = (uint32_t)(t - (uint64_t)j * blocks);
+    // warps walk the 32-word blocks of one product after the other (j advances
+    // when blk wraps): no 64-bit division per task
+    const uint32_t wstep = gridDim.x * (blockDim.x / 32);
+    uint32_t wid = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    uint32_t j = wid / blocks, blk = wid - j * blocks;
+    const uint32_t jstep = wstep / blocks, bstep = wstep - jstep * blocks;
+    for (; j < count; j += jstep, blk += bstep) {
+        if (blk >= blocks) {
+            blk -= blocks;
+            ++j;
+            if (j >= count)
+                break;
+        }
         const uint32_t w0 = blk * 32u;
         const uint32_t *row = qbits + (size_t)j * qwords;
-        // q run: start = (Q_e - w0 - 31) mod n, 32 bits
-        const uint32_t start = (uint32_t)(((uint64_t)Qe + 32ull * n - (w0 % n) - 31u) % n);
+        // q run: start = (Q_e - w0 - 31) mod n, 32 bits (n <= 65535: 32-bit arithmetic)
+        const uint32_t start = (Qe + 32u * n - (w0 % n) - 31u) % n;
         uint32_t x;
         if (start + 31u < n) {
             const uint32_t lo = row[start >> 5], hi = row[(start >> 5) + 1u];
@@ -516,7 +537,7 @@ cudaError_t launch_tc_group(const uint64_t *b, size_t stride_b, uint64_t *out, s
     if (e != cudaSuccess)
         return e;
     const uint64_t tasks = (uint64_t)count * (((n + 31) / 32 + 31) / 32);
-    tc_assemble_kernel<<<(unsigned)std::min<uint64_t>(8ull * sm_count, (tasks + 7) / 8), 256, 0, st>>>(
+    tc_assemble_kernel<<<(unsigned)std::min<uint64_t>(16ull * sm_count, (tasks + 7) / 8), 256, 0, st>>>(
         qbits, sh.qwords, n, sh.inv32, count, out, stride_out);
     return cudaGetLastError();
 }
