@@ -445,13 +445,14 @@ __global__ void __launch_bounds__(256) tc_assemble_kernel(const uint32_t *__rest
                 q = q + 1u == n ? 0u : q + 1u;
             }
         }
-        x = __brev(x);   // bit i <-> word w0 + i
-        uint32_t mine = 0;
+        // lane e holds bit e of words w0 .. w0+31 (bit i <-> word w0 + i);
+        // a 32 x 32 bit transpose across the warp (swap the off-diagonal
+        // s x s blocks for s = 16, 8, 4, 2, 1) leaves word w0 + lane in lane
+        uint32_t mine = __brev(x);
 #pragma unroll
-        for (uint32_t i = 0; i < 32u; ++i) {
-            const uint32_t col = __ballot_sync(0xffffffffu, (x >> i) & 1u);   // word w0 + i, bit e from lane e
-            if (lane == i)
-                mine = col;
+        for (uint32_t sh = 16, m = 0x0000ffffu; sh > 0; sh >>= 1, m ^= m << sh) {
+            const uint32_t y = __shfl_xor_sync(0xffffffffu, mine, sh);
+            mine = (lane & sh) ? ((mine & ~m) | ((y >> sh) & m)) : ((mine & m) | ((y << sh) & ~m));
         }
         const uint32_t w = w0 + lane;
         if (w < L32) {
