@@ -238,6 +238,24 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def measured_tc_traffic(n: int, count: int):
+    """DRAM bytes of one tensor-core GEMM launch from the committed ncu summary
+    (profiles/traffic.txt: "tc-shared-<n>-<count> tc <tc_source_hash> bytes"),
+    or None if the kernel changed since the counters were taken."""
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2201_10473_gb300", "csrc", "tc_circulant.cu"), "rb") as fh:
+        h = hashlib.sha256(fh.read()).hexdigest()[:16]
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
+            for line in f:
+                parts = line.split("#", 1)[0].split()
+                if len(parts) == 4 and parts[0] == f"tc-shared-{n}-{count}" and parts[1] == "tc" and parts[2] == h:
+                    return float(parts[3])
+    except OSError:
+        pass
+    return None
+
+
 def measured_traffic(workload: str, spec: str):
     """DRAM bytes per launch from the committed ncu summary (profiles/traffic.txt:
     "workload plan kernel_source_hash dram_bytes_per_launch"), or None if the
@@ -705,24 +723,55 @@ def run_shared(device):
         r = it[0] % R
         it[0] += 1
         ctx.mul_strided(a_of(r), dv[r], n, True, out=out, persistent=True)
+    def call_tc():
+        r = it[0] % R
+        it[0] += 1
+        ctx.mulmod_shared_tc(dh, dv[r], n, out=out)
     rates = {}
-    for rep in range(3):        # interleaved: shared, unshared, shared, ...
+    ms_tc = []
+    for rep in range(3):        # interleaved: shared, unshared, tensor cores, shared, ...
         for name, a_of in (("shared", lambda r: dh), ("unshared", lambda r: dhs)):
             it[0] = 0
             ms = _time_calls(lambda: call(a_of), 40, 3)
             rates.setdefault(name, []).append(count / (ms * 1e-3))
+        it[0] = 0
+        ms_tc.append(_time_calls(call_tc, 40, 3))
+    sample = np.arange(0, count, 512)
+    exp = np.stack([oracle.mulmod(h[0], vecs[0][p], n) for p in sample])
     it[0] = 0
     call(lambda r: dh)
-    sample = np.arange(0, count, 512)
-    ok = bool(np.array_equal(_host(out)[sample], np.stack([oracle.mulmod(h[0], vecs[0][p], n) for p in sample])))
+    ok = bool(np.array_equal(_host(out)[sample], exp))
+    it[0] = 0
+    out.zero_()
+    call_tc()
+    ok_tc = bool(np.array_equal(_host(out)[sample], exp))
+    ctx.sync_status()
     plan = ctx.get_plan(n)
     ctx.close()
     shared, unshared = max(rates["shared"]), max(rates["unshared"])
+    ms = min(ms_tc)
+    # roofline of the tensor-core call: the n^2 multiply-adds of each product
+    # (2 n^2 flops), over the whole call (its GEMM kernel is ~91% of it in the
+    # ncu launch list), against the fp4 dense peak taken as the measured bf16
+    # burst x the nominal fp4/bf16 ratio (13.5 / 2.25 = 6)
+    flops = 2.0 * n * n * count
+    peak = None
+    try:
+        with open(PEAKS_FILE) as f:
+            peak = json.load(f)["bf16_tflops"] * 6.0
+    except (OSError, KeyError, ValueError):
+        peak = 1900.0 * 6.0
+    achieved = flops / (ms * 1e-3) / 1e12
     return {"workload": "shared-key-17669-mulmod", "products": count, "plan": plan,
             "shared_mults_per_s": shared, "unshared_mults_per_s": unshared, "shared_over_unshared": shared / unshared,
-            "note": "one a for every product (GF2X_BATCH_SHARED_A); the product is ALU-bound, so sharing saves "
-                    "memory reads, not time",
-            "sample_checked_against_oracle": ok}
+            "tensor_core_mults_per_s": count / (ms * 1e-3), "tensor_over_shared_comb": count / (ms * 1e-3) / shared,
+            "tensor_core_roofline": {"bound": "tensor", "dtype": "fp4 e2m1 (0/1), fp32 counts", "achieved": achieved,
+                                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                                     "peak_note": "MEASURED_PEAKS bf16_tflops x 6 (nominal fp4/bf16); whole call timed",
+                                     "traffic": measured_tc_traffic(n, count)},
+            "note": "one a for every product: GF2X_BATCH_SHARED_A on the comb path (ALU-bound: sharing saves memory "
+                    "reads, not time), and gf2x_mulmod_shared_tc, the circulant GEMM on the tensor cores",
+            "sample_checked_against_oracle": ok and ok_tc}
 
 
 def run_unbalanced(device):
