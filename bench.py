@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the other workloads (C1, C3, C4, shared key, unbalanced, sparse, Toom-4, C5)")
     p.add_argument("--serving-requests", type=int, default=200000)
     p.add_argument("--plan", default=None, help="plan spec for the main workload (default: the tuned database)")
+    p.add_argument("--only-extra", default=None, choices=sorted(EXTRAS),
+                   help="run one of the other workloads alone and print its JSON (for profiling runs)")
     return p.parse_args()
 
 
@@ -989,12 +991,17 @@ def run_c5(device, requests):
     return out
 
 
-def run_extras(args, device):
+EXTRAS = ("c1", "c3", "c4", "shared_key", "unbalanced", "sparse_ct", "toom4", "c5")
+
+
+def run_extras(args, device, only=None):
     res = {}
     for name, fn in (("c1", lambda: run_c1(device)), ("c3", lambda: run_c3(device)), ("c4", lambda: run_c4(device)),
                      ("shared_key", lambda: run_shared(device)), ("unbalanced", lambda: run_unbalanced(device)),
                      ("sparse_ct", lambda: run_sparse(device)), ("toom4", lambda: run_toom4(device)),
                      ("c5", lambda: run_c5(device, args.serving_requests))):
+        if only and name != only:
+            continue
         t0 = time.time()
         try:
             res[name] = fn()
@@ -1007,6 +1014,11 @@ def run_extras(args, device):
 def main():
     args = parse()
     w = WORKLOADS[args.workload]
+    if args.only_extra:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(run_extras(args, 0, only=args.only_extra)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, w)
     else:
