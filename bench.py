@@ -576,32 +576,49 @@ def run_c3(device):
     by_size = np.argsort(-sizes, kind="stable")
     items_lf = items[torch.from_numpy(by_size).cuda()].contiguous()
     log = autotune.packaged_log()
-    best = None
-    for plans in autotune.mixed_plan_sets(log, weights, 2048, top=3):
+
+    def time_mixed(plans):
+        """One graph-replayed persistent launch over the device items: as
+        interleaved (static stride), largest first (static stride), largest
+        first with CTAs taking items from a counter (dynamic)."""
         ctx = Context(device, plan_db=None)
         for n, sp in plans.items():
             ctx.set_plan(int(n), sp)
         ctx.prepare(sorted(int(n) for n in weights))
         stream = torch.cuda.Stream()
-        with torch.cuda.stream(stream):
-            ctx.mul_batched_device(items, len(sizes), persistent=True)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=stream):
-            ctx.mul_batched_device(items, len(sizes), persistent=True)
-        ms = _time_calls(g.replay, 10, 3)
-        with torch.cuda.stream(stream):
-            ctx.mul_batched_device(items_lf, len(sizes), persistent=True)
-        torch.cuda.synchronize()
-        g_lf = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g_lf, stream=stream):
-            ctx.mul_batched_device(items_lf, len(sizes), persistent=True)
-        ms_lf = _time_calls(g_lf.replay, 10, 3)
+        res = []
+        for its, dyn in ((items, False), (items_lf, False), (items_lf, True)):
+            with torch.cuda.stream(stream):
+                ctx.mul_batched_device(its, len(sizes), persistent=True, dynamic=dyn)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                ctx.mul_batched_device(its, len(sizes), persistent=True, dynamic=dyn)
+            res.append(_time_calls(g.replay, 10, 3))
         ctx.sync_status()
-        if best is None or ms_lf < best[2]:
-            best = (ms, plans, ms_lf)
         ctx.close()
+        return res
+
+    # plan sets: (i) from the exhaustive measured log, (ii) proposed by the
+    # learned cost model trained on that log; the measured best of (i)
+    # judges the regret of (ii)
+    from paper_2201_10473_gb300 import costmodel
+    measured_sets = autotune.mixed_plan_sets(log, weights, 2048, top=3)
+    model = costmodel.CostModel(seed=0)
+    model.fit(log, steps=3000, seed=0)
+    model_sets = autotune.model_mixed_plan_sets(model, weights, 2048, top=3)
+    timed = []
+    for origin, sets in (("log", measured_sets), ("model", model_sets)):
+        for plans in sets:
+            t = time_mixed(plans)
+            timed.append((min(t), origin, plans, t))
+    best_log = min((x for x in timed if x[1] == "log"), key=lambda x: x[0])
+    best_model = min((x for x in timed if x[1] == "model"), key=lambda x: x[0])
+    _, _, plans, (ms, ms_lf, ms_dyn) = min(timed, key=lambda x: x[0])
+    model_regret = best_model[0] / best_log[0] - 1.0
+    best = (ms, plans, min(ms_lf, ms_dyn))
     ms, plans, ms_lf = best
+    dyn_best = ms_dyn <= ms_lf
     # recompute with the best set and check a sample against the oracle
     ctx = Context(device, plan_db=None)
     for n, sp in plans.items():
@@ -609,7 +626,7 @@ def run_c3(device):
     ctx.prepare(sorted(int(n) for n in weights))
     for o in outs.values():
         o.zero_()
-    ctx.mul_batched_device(items_lf, len(sizes), persistent=True)
+    ctx.mul_batched_device(items_lf, len(sizes), persistent=True, dynamic=dyn_best)
     torch.cuda.synchronize()
     ok = True
     for r in range(0, len(sizes), 149):
@@ -670,6 +687,13 @@ def run_c3(device):
     return {"workload": wk.name, "products": total, "plans": {str(k): v for k, v in plans.items()},
             "one_launch_graph_mults_per_s": total / (ms * 1e-3),
             "one_launch_graph_largest_first_mults_per_s": total / (ms_lf * 1e-3),
+            "one_launch_schedule": "largest first, items from a counter" if dyn_best else "largest first, static stride",
+            "plan_sets_timed": [{"origin": o, "plans": {str(k): v for k, v in p.items()},
+                                 "interleaved_ms": t[0], "largest_first_ms": t[1], "largest_first_dynamic_ms": t[2]}
+                                for _, o, p, t in timed],
+            "model_proposed_best_mults_per_s": total / (best_model[0] * 1e-3),
+            "log_best_mults_per_s": total / (best_log[0] * 1e-3),
+            "model_regret_vs_measured_log": model_regret,
             "plain_mults_per_s": total / (ms_plain * 1e-3),
             "per_size_launches_mults_per_s": total / (ms_grouped * 1e-3),
             "one_graph_concurrent_per_size_kernels_mults_per_s": total / (ms_graph * 1e-3),

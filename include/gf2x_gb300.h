@@ -64,6 +64,7 @@ typedef enum {
 #define GF2X_BATCH_ITEMS_ON_DEVICE 2u /* `items` points to device memory (gf2x_item array) */
 #define GF2X_BATCH_LARGEST_FIRST 4u   /* order items by decreasing n (sizes are public) before the launch */
 #define GF2X_BATCH_SHARED_A 8u        /* gf2x_mul_strided: one a for every product (a fixed key polynomial) */
+#define GF2X_BATCH_DYNAMIC 16u        /* gf2x_mul_batched, persistent: CTAs take items in order from a counter */
 
 /*
  * A recursion plan: `nlev` split levels from the top down, then a leaf of
@@ -247,7 +248,14 @@ gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, co
  *    looping over items i, i + grid, i + 2 grid, ...; otherwise one CTA per
  *    item.  Items of uneven sizes balance best ordered largest first (every
  *    CTA then draws one item of each size band per round).
- *  - GF2X_BATCH_LARGEST_FIRST (host items): larger n first. */
+ *  - GF2X_BATCH_LARGEST_FIRST (host items): larger n first.
+ *  - GF2X_BATCH_DYNAMIC (with GF2X_BATCH_PERSISTENT): each CTA takes its
+ *    next item from a device counter of the context (zeroed by a memset on
+ *    `stream` before the launch, which a CUDA graph captures as well), so
+ *    items are started in array order as CTAs free up -- with items sorted
+ *    largest first this is longest-processing-time-first scheduling.  The
+ *    context has 256 counters used round robin: more than 256 dynamic
+ *    launches in flight at once on different streams would share one. */
 gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, size_t count,
                              uint32_t batch_flags, gf2x_stream stream);
 

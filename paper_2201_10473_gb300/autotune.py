@@ -247,6 +247,33 @@ def mixed_plan_sets(records: list, weights: dict, batch: int, top: int = 3) -> l
     return [plans for _, plans in scored[:top]]
 
 
+def model_mixed_plan_sets(model, weights: dict, batch: int, top: int = 3, cands: dict | None = None) -> list:
+    """Candidate plan sets for ONE launch over several sizes, proposed by the
+    learned cost model (costmodel.CostModel) instead of measurements: every
+    in-CTA candidate of every size is scored by the network, and for each
+    (leaf size, CTA threads) pair the set takes each size's best-scored plan;
+    sets are ranked by the count-weighted predicted time.  Only the first
+    `top` are then measured as real launches."""
+    best = {}   # (n, S, threads) -> (predicted ns per product, spec)
+    for n in weights:
+        specs = [c for c in (cands[n] if cands else candidate_specs(n)) if c.split("/")[5:6] != ["1"]]
+        pred = model.predict(n, batch, specs)
+        for spec, y in zip(specs, pred):
+            info = gf2x.plan_info(n, spec)
+            key = (n, info["leaf_words"], info["threads"])
+            ns = 2.0 ** float(y)
+            if key not in best or ns < best[key][0]:
+                best[key] = (ns, spec)
+    pairs = {(S, t) for (_, S, t) in best}
+    scored = []
+    for S, t in pairs:
+        if all((n, S, t) in best for n in weights):
+            cost = sum(w * best[(n, S, t)][0] for n, w in weights.items())
+            scored.append((cost, {n: best[(n, S, t)][1] for n in weights}))
+    scored.sort(key=lambda x: x[0])
+    return [plans for _, plans in scored[:top]]
+
+
 PACKAGED_TIMING_LOG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans", "gb300_timing_log.jsonl.gz")
 # exhaustive search of one product per launch (batch 1): the single-product plans
 PACKAGED_SINGLE_LOG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans",

@@ -35,6 +35,7 @@ struct PlanEntry {
 
 constexpr uint64_t kWorkspaceCap = 256ull << 20;  // split plans run in chunks of at most this much scratch
 constexpr size_t kFixedStagingItems = 16384;      // item staging per ring buffer in a fixed-workspace context
+constexpr uint32_t kCounters = 256;               // work counters of dynamic launches (reused round robin)
 
 // Allocation failures injected on the host (tests of the GF2X_ENOMEM paths):
 // the next g_fail_allocs allocations of any context fail without a CUDA call.
@@ -94,6 +95,8 @@ struct gf2x_ctx {
     cudaEvent_t ub_done = nullptr;                      // recorded after the last use of ub
     cudaStream_t ub_stream = nullptr;
     bool ub_used = false;
+    uint32_t *counters = nullptr;                       // work counters of dynamic launches (a ring)
+    uint32_t counter_next = 0;
     bool fixed = false;                                 // workspace fixed at creation: compute calls allocate nothing
     void *arena = nullptr;                              // the fixed workspace (split | unbalanced/Toom | host pipeline)
     uint64_t allocs = 0;                                // device and pinned allocations made by the context
@@ -218,6 +221,7 @@ extern "C" gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device, size_t worksp
         e = cudaMemset(ctx->err_dev, 0, sizeof(uint32_t));
     alloc((void **)&ctx->plan_of_n_host, sizeof(uint32_t) * (GF2X_MAX_N + 1), true);
     alloc((void **)&ctx->plan_of_n_dev, sizeof(uint32_t) * (GF2X_MAX_N + 1), false);
+    alloc((void **)&ctx->counters, sizeof(uint32_t) * kCounters, false);
     if (e == cudaSuccess) {
         memset(ctx->plan_of_n_host, 0xff, sizeof(uint32_t) * (GF2X_MAX_N + 1));
         e = cudaMemset(ctx->plan_of_n_dev, 0xff, sizeof(uint32_t) * (GF2X_MAX_N + 1));
@@ -330,6 +334,8 @@ extern "C" void gf2x_ctx_destroy(gf2x_ctx *ctx)
         cudaFreeHost(ctx->plan_of_n_host);
     if (ctx->plan_of_n_dev)
         cudaFree(ctx->plan_of_n_dev);
+    if (ctx->counters)
+        cudaFree(ctx->counters);
     if (ctx->arena) {   // ws, ub and hp.buf live in it
         cudaFree(ctx->arena);
     } else {
@@ -541,7 +547,7 @@ static gf2x_status check_operands(gf2x_ctx *ctx, const uint64_t *out, const uint
 }
 
 static gf2x_status launch(gf2x_ctx *ctx, const LaunchArgs &args, uint32_t S, unsigned threads, size_t smem,
-                          size_t count, bool persistent, cudaStream_t stream)
+                          size_t count, bool persistent, cudaStream_t stream, bool dynamic = false)
 {
     LaunchFn fn = launcher_for(S);
     if (!fn)
@@ -565,6 +571,13 @@ static gf2x_status launch(gf2x_ctx *ctx, const LaunchArgs &args, uint32_t S, uns
             return fail(ctx, GF2X_EUNSUPPORTED, "kernel does not fit on an SM");
         grid = (unsigned)std::min<size_t>(count, (size_t)per_sm * ctx->sm_count);
         a.persistent = 1;
+        if (dynamic && grid > 0) {   // items in order from a counter zeroed on the stream (a graph node too)
+            uint32_t *c = ctx->counters + (ctx->counter_next++ % kCounters);
+            cudaError_t e = cudaMemsetAsync(c, 0, sizeof(uint32_t), stream);
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e, "work counter reset");
+            a.work_counter = c;
+        }
     } else {
         if (count > 0x7fffffffu)
             return fail(ctx, GF2X_EINVAL, "batch too large for one launch");
@@ -1304,8 +1317,10 @@ extern "C" gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, s
         return GF2X_OK;
     if (!items)
         return fail(ctx, GF2X_EINVAL, "null item array");
-    if (batch_flags & ~(uint32_t)(GF2X_BATCH_PERSISTENT | GF2X_BATCH_ITEMS_ON_DEVICE | GF2X_BATCH_LARGEST_FIRST))
+    if (batch_flags & ~(uint32_t)(GF2X_BATCH_PERSISTENT | GF2X_BATCH_ITEMS_ON_DEVICE | GF2X_BATCH_LARGEST_FIRST |
+                                  GF2X_BATCH_DYNAMIC))
         return fail(ctx, GF2X_EINVAL, "unknown batch flag");
+    const bool dynamic = (batch_flags & GF2X_BATCH_DYNAMIC) != 0;
     if (count > 0xffffffffull)
         return fail(ctx, GF2X_EINVAL, "batch too large");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1341,7 +1356,7 @@ extern "C" gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, s
         args.mode = kItemsUser;
         args.err = ctx->err_dev;
         args.plan_of_n = ctx->plan_of_n_dev;
-        return launch(ctx, args, S, threads, 4ull * smem_words, count, persistent, s);
+        return launch(ctx, args, S, threads, 4ull * smem_words, count, persistent, s, dynamic);
     }
 
     if (ctx->fixed && count > kFixedStagingItems) {   // pieces that fit the fixed item staging
@@ -1431,7 +1446,7 @@ extern "C" gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, s
         args.count = (uint32_t)(g1 - g0);
         args.mode = kItemsArray;
         args.err = ctx->err_dev;
-        st = launch(ctx, args, S, threads, 4ull * smem_words, g1 - g0, persistent, s);
+        st = launch(ctx, args, S, threads, 4ull * smem_words, g1 - g0, persistent, s, dynamic);
         if (st != GF2X_OK)
             return st;
         g0 = g1;

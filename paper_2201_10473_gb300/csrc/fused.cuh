@@ -723,33 +723,53 @@ fused_mul_kernel(const LaunchArgs args)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ GPlan P;
+    __shared__ uint32_t next_item;
     const uint32_t smem_avail = dynamic_smem_bytes();
     const uint32_t step = args.persistent ? gridDim.x : args.count;
     uint32_t loaded = kEmptyItem;   // plan slot currently in P (none)
-    for (uint32_t i = blockIdx.x; i < args.count; i += step) {
+    uint32_t i = blockIdx.x;
+    if (args.work_counter) {   // dynamic order: items are taken from the counter (sizes only decide the cost)
+        if (threadIdx.x == 0)
+            next_item = atomicAdd(args.work_counter, 1u);
+        __syncthreads();
+        i = next_item;
+    }
+    while (i < args.count) {
         const DevItem it = fetch_item(args, i);
+        bool run = true;
         if (it.plan >= kEmptyItem) {  // uniform over the CTA: every thread read the same item
             if (it.plan == kNoPlan && threadIdx.x == 0)
                 flag_error(args.err, kErrNoPlan);
-            continue;
+            run = false;
+        } else {
+            __syncthreads();   // the previous product is done with shared memory
+            if (it.plan != loaded) {   // uniform: a persistent CTA of a uniform batch loads its plan once
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(args.plans + it.plan);
+                uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
+                for (uint32_t w = threadIdx.x; w < sizeof(GPlan) / 4; w += blockDim.x)
+                    dst[w] = __ldg(src + w);
+                loaded = it.plan;
+                __syncthreads();
+            }
+            // a plan made for another leaf size or more shared memory than this
+            // launch has is refused (uniform over the CTA), never run
+            if (P.S != (uint32_t)S || 4u * P.smem_words > smem_avail || P.nlev > (uint32_t)kMaxLevels) {
+                if (threadIdx.x == 0)
+                    flag_error(args.err, kErrPlanMismatch);
+                run = false;
+            }
         }
-        __syncthreads();   // the previous product is done with shared memory
-        if (it.plan != loaded) {   // uniform: a persistent CTA of a uniform batch loads its plan once
-            const uint32_t *src = reinterpret_cast<const uint32_t *>(args.plans + it.plan);
-            uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
-            for (uint32_t w = threadIdx.x; w < sizeof(GPlan) / 4; w += blockDim.x)
-                dst[w] = __ldg(src + w);
-            loaded = it.plan;
-            __syncthreads();
-        }
-        // a plan made for another leaf size or more shared memory than this
-        // launch has is refused (uniform over the CTA), never run
-        if (P.S != (uint32_t)S || 4u * P.smem_words > smem_avail || P.nlev > (uint32_t)kMaxLevels) {
+        if (run)
+            run_product<S>(P, it, sm, args.err);
+        if (args.work_counter) {
+            __syncthreads();   // every thread has read next_item
             if (threadIdx.x == 0)
-                flag_error(args.err, kErrPlanMismatch);
-            continue;
+                next_item = atomicAdd(args.work_counter, 1u);
+            __syncthreads();
+            i = next_item;
+        } else {
+            i += step;
         }
-        run_product<S>(P, it, sm, args.err);
     }
 }
 

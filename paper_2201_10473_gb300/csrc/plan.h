@@ -94,6 +94,7 @@ struct LaunchArgs {
     uint32_t shared_a;        // mode kItemsStrided: 1 = every product reads the same a
     uint32_t *err;            // device error word (checked mode), may be null
     const uint32_t *plan_of_n; // mode kItemsUser: plan slot of every n (kNoPlan if none)
+    uint32_t *work_counter;   // non-null: persistent CTAs take items in order from this counter (zeroed before the launch)
 };
 
 // kItemsUser: the items are the caller's gf2x_item array on the device, whose

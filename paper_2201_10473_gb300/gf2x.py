@@ -28,6 +28,7 @@ BATCH_PERSISTENT = 1
 BATCH_ITEMS_ON_DEVICE = 2
 BATCH_LARGEST_FIRST = 4
 BATCH_SHARED_A = 8
+BATCH_DYNAMIC = 16
 
 STATUS = {0: "GF2X_OK", 1: "GF2X_EINVAL", 2: "GF2X_ENOMEM", 3: "GF2X_ECUDA", 4: "GF2X_ETIMEOUT",
           5: "GF2X_EUNSUPPORTED", 6: "GF2X_EBUSY", 7: "GF2X_EDEVICE"}
@@ -437,20 +438,25 @@ class Context:
                                                 _stream_handle(stream)), "gf2x_mul_strided_host")
         return out
 
-    def mul_batched(self, items, persistent: bool = False, largest_first: bool = False, stream=None):
-        """items: list of (a, b, out, n, reduce) with CUDA tensors; one launch per leaf size."""
+    def mul_batched(self, items, persistent: bool = False, largest_first: bool = False, stream=None,
+                    dynamic: bool = False):
+        """items: list of (a, b, out, n, reduce) with CUDA tensors; one launch per leaf size.
+        dynamic (persistent only): CTAs take items in order from a counter."""
         arr = (Item * len(items))()
         for i, (a, b, out, n, reduce) in enumerate(items):
             _check_operand(a, n, "a")
             _check_operand(b, n, "b")
             arr[i] = Item(a.data_ptr(), b.data_ptr(), out.data_ptr(), n, REDUCE if reduce else 0)
-        flags = (BATCH_PERSISTENT if persistent else 0) | (BATCH_LARGEST_FIRST if largest_first else 0)
+        flags = (BATCH_PERSISTENT if persistent else 0) | (BATCH_LARGEST_FIRST if largest_first else 0) | \
+            (BATCH_DYNAMIC if dynamic else 0)
         self._raise(lib().gf2x_mul_batched(self._h, ctypes.cast(arr, ctypes.c_void_p), len(items), flags,
                                            _stream_handle(stream)), "gf2x_mul_batched")
 
-    def mul_batched_device(self, items_dev: torch.Tensor, count: int, persistent: bool = True, stream=None):
-        """items_dev: a CUDA tensor holding `count` packed gf2x_item records (see pack_items)."""
-        flags = BATCH_ITEMS_ON_DEVICE | (BATCH_PERSISTENT if persistent else 0)
+    def mul_batched_device(self, items_dev: torch.Tensor, count: int, persistent: bool = True, stream=None,
+                           dynamic: bool = False):
+        """items_dev: a CUDA tensor holding `count` packed gf2x_item records (see pack_items).
+        dynamic (persistent only): CTAs take items in array order from a counter."""
+        flags = BATCH_ITEMS_ON_DEVICE | (BATCH_PERSISTENT if persistent else 0) | (BATCH_DYNAMIC if dynamic else 0)
         self._raise(lib().gf2x_mul_batched(self._h, items_dev.data_ptr(), count, flags, _stream_handle(stream)),
                     "gf2x_mul_batched(device)")
 

@@ -54,7 +54,8 @@ def test_experiment_libraries_load_and_export_their_test_entries():
 def test_binding_flags_match_the_header():
     text = open(os.path.join(ROOT, "include", "gf2x_gb300.h")).read()
     defines = {m.group(1): int(m.group(2), 0) for m in re.finditer(r"#define GF2X_([A-Z_]+)\s+\(?([0-9x]+)u", text)}
-    for name in ("REDUCE", "BATCH_PERSISTENT", "BATCH_ITEMS_ON_DEVICE", "BATCH_LARGEST_FIRST", "BATCH_SHARED_A"):
+    for name in ("REDUCE", "BATCH_PERSISTENT", "BATCH_ITEMS_ON_DEVICE", "BATCH_LARGEST_FIRST", "BATCH_SHARED_A",
+                 "BATCH_DYNAMIC"):
         assert getattr(gf2x, name) == defines[name], name
     assert gf2x.HOST_INPUTS_READY == 1 << 8 and "HOST_INPUTS_READY" in text
     batch = [v for k, v in defines.items() if k.startswith("BATCH_")]
