@@ -606,7 +606,7 @@ def run_c3(device):
     measured_sets = autotune.mixed_plan_sets(log, weights, 2048, top=3)
     model = costmodel.CostModel(seed=0)
     model.fit(log, steps=3000, seed=0)
-    model_sets = autotune.model_mixed_plan_sets(model, weights, 2048, top=3)
+    model_sets = autotune.model_mixed_plan_sets(model, weights, 2048, top=6)
     timed = []
     for origin, sets in (("log", measured_sets), ("model", model_sets)):
         for plans in sets:
@@ -961,7 +961,10 @@ def run_c5(device, requests):
     srv = serve.Server(ctx, weights, budget, max_batch=2048, streams=3, use_graphs=True)
     closed = srv.run(reqs, np.zeros(len(sizes)))
     cap = closed.completed / closed.wall_s
-    out = {"workload": wk.name, "requests": len(sizes), "budget_bytes": budget, "plans": {str(k): v for k, v in plans.items()},
+    out = {"workload": wk.name, "requests": len(sizes), "budget_bytes": budget,
+           "budget_covers": "request slots (both operands, copied in on admission, and the result) and the "
+                            "servers' item and copy lists; device-item launches use no other scratch",
+           "plans": {str(k): v for k, v in plans.items()},
            "closed_loop": closed.summary(), "loads": {}}
     for f in (0.5, 0.8, 0.95, 1.2):
         arr = wl.poisson_arrivals(wk.seed + int(f * 100), len(sizes), f * cap)
@@ -1000,8 +1003,8 @@ def run_c5(device, requests):
     out["tight_budget_4MiB_load_0.95"] = dict(r.summary(), offered_per_s=0.95 * cap,
                                             slots=sum(tight.pool.capacity.values()))
     ctx.sync_status()
-    # plain per-request launches on a subset
-    m = min(4000, len(sizes))
+    # plain per-request launches (each copies its operands into its slot, then one launch), every request
+    m = len(sizes)
     sub_reqs = serve.RequestSet(reqs.sizes[:m], reqs.index[:m], reqs.a, reqs.b)
     pool = serve.SlotPool(weights, budget)
     # (the single-product plans, tuned for one launch at a time, serve three

@@ -125,6 +125,13 @@ typedef struct {
     uint32_t flags;              /* GF2X_REDUCE or 0 */
 } gf2x_item;
 
+/* One row copy of gf2x_copy_rows (device pointers, 8-byte aligned). */
+typedef struct {
+    const uint64_t *src;
+    uint64_t *dst;
+    uint64_t limbs;              /* 0: an empty entry (padding) */
+} gf2x_copy_row;
+
 typedef struct gf2x_ctx gf2x_ctx;
 typedef void *gf2x_stream;       /* cudaStream_t */
 
@@ -418,6 +425,14 @@ gf2x_status gf2x_ctx_prepare(gf2x_ctx *ctx, const uint32_t *sizes, size_t count,
  * memory, resident CTAs per SM and the SM count (any pointer may be NULL). */
 gf2x_status gf2x_ctx_launch_shape(gf2x_ctx *ctx, uint32_t n, uint32_t *threads, uint32_t *smem_bytes,
                                   uint32_t *blocks_per_sm, uint32_t *sm_count);
+
+/* `count` row copies in one launch on `stream`: entry i of the DEVICE array
+ * `rows` copies rows[i].limbs 64-bit words from rows[i].src to rows[i].dst
+ * (ranges must not overlap; entries with limbs = 0 are skipped).  Nothing is
+ * checked or copied on the host, so the call can be captured in a CUDA
+ * graph.  The paper has no counterpart: the serving loop uses it to stage
+ * the operands of the requests it admits into its device-memory budget. */
+gf2x_status gf2x_copy_rows(gf2x_ctx *ctx, const gf2x_copy_row *rows, size_t count, gf2x_stream stream);
 
 /* Wait for `stream`, then report and clear any checked-mode violation
  * (GF2X_EDEVICE) or asynchronous CUDA error (GF2X_ECUDA). */

@@ -1478,6 +1478,18 @@ extern "C" gf2x_status gf2x_ctx_sync_status(gf2x_ctx *ctx, gf2x_stream stream)
     return GF2X_OK;
 }
 
+extern "C" gf2x_status gf2x_copy_rows(gf2x_ctx *ctx, const gf2x_copy_row *rows, size_t count, gf2x_stream stream)
+{
+    if (!ctx)
+        return GF2X_EINVAL;
+    if (count == 0)
+        return GF2X_OK;
+    if (!rows)
+        return fail(ctx, GF2X_EINVAL, "null row list");
+    cudaError_t e = launch_copy_rows(rows, count, ctx->sm_count, (cudaStream_t)stream);
+    return e == cudaSuccess ? GF2X_OK : cuda_fail(ctx, e, "row copy launch");
+}
+
 extern "C" gf2x_status gf2x_ctx_wait(gf2x_ctx *ctx, gf2x_stream stream, uint32_t timeout_ms)
 {
     if (!ctx)

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "gf2x_gb300.h"
 #include "plan.h"
 
 namespace gf2x {
@@ -83,6 +84,9 @@ cudaError_t launch_tc_rseq(const uint64_t *a, uint32_t n, const TcShape &sh, uin
 cudaError_t launch_tc_group(const uint64_t *b, size_t stride_b, uint64_t *out, size_t stride_out, uint32_t n,
                             uint32_t count, const TcShape &sh, const uint8_t *rseq, uint8_t *scratch, uint32_t *err,
                             int sm_count, cudaStream_t st);
+
+// row copies of the serving loop (copy_rows.cu)
+cudaError_t launch_copy_rows(const gf2x_copy_row *rows, size_t count, int sm_count, cudaStream_t st);
 
 typedef cudaError_t (*LaunchFn)(const LaunchArgs &, unsigned, unsigned, size_t, cudaStream_t);
 typedef cudaError_t (*PrepareFn)(int *, unsigned, size_t);

@@ -76,6 +76,7 @@ _SIGNATURES = {
     "gf2x_ctx_alloc_count": ([_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], _I),
     "gf2x_debug_fail_next_allocs": ([_U32], _U32),
     "gf2x_ctx_wait": ([_P, _P, _U32], _I),
+    "gf2x_copy_rows": ([_P, _P, _SZ, _P], _I),
     "gf2x_ctx_destroy": ([_P], None),
     "gf2x_ctx_set_plan": ([_P, _U32, ctypes.POINTER(PlanSpec)], _I),
     "gf2x_ctx_get_plan": ([_P, _U32, ctypes.POINTER(PlanSpec)], _I),
@@ -274,6 +275,11 @@ class Context:
         if st not in (0, 4):
             self._raise(st, "wait")
         return st
+
+    def copy_rows(self, rows_dev: torch.Tensor, count: int, stream=None):
+        """rows_dev: a CUDA int64 tensor of `count` (src, dst, limbs) triples (gf2x_copy_row)."""
+        self._raise(lib().gf2x_copy_rows(self._h, rows_dev.data_ptr(), count, _stream_handle(stream)),
+                    "gf2x_copy_rows")
 
     def alloc_count(self) -> tuple[int, int]:
         """(device + pinned allocations, their bytes) made by this context so far."""

@@ -3,8 +3,14 @@
 Requests (n, a, b) arrive over time with their operands already resident on
 the device.  The loop
 
-  * admits a request when an output slot of its size is free in a fixed HBM
-    budget (a device arena carved into per-size slots), else it waits;
+  * admits a request when a request slot of its size is free in a fixed HBM
+    budget (a device arena carved into per-size slots, each holding the
+    request's two operands and its result), else it waits; an admitted
+    request's operands are copied into its slot (one gf2x_copy_rows launch
+    per batch, in the same captured graph as the products) and the slot is
+    freed when the request retires, so operands and results both count
+    against the budget, together with the server's item and copy lists
+    (device-item launches use no other scratch);
   * keeps up to `streams` batches in flight, one per CUDA stream; whenever a
     stream is free it launches everything admitted so far (up to max_batch)
     as ONE persistent launch over a device item array, replayed from a CUDA
@@ -74,24 +80,32 @@ def make_requests(sizes, operand_fn) -> RequestSet:
 
 
 class SlotPool:
-    """Output slots of every size class carved from one arena of budget_bytes.
+    """Request slots of every size class carved from one arena of budget_bytes.
 
-    The free slots of a size are a stack of addresses (free[n][:top[n]]), so
-    that a batch takes or returns all of its slots in one array operation."""
+    A slot of size n holds the request's operands a and b and its result r,
+    each part ceil(n/64) limbs rounded up to an even count (16-byte aligned):
+    a at the slot address, b one part later, r two parts later (operands=False:
+    result slots only).  The free slots of a size are a stack of addresses
+    (free[n][:top[n]]), so that a batch takes or returns all of its slots in
+    one array operation."""
 
-    def __init__(self, sizes: dict, budget_bytes: int, device="cuda"):
+    def __init__(self, sizes: dict, budget_bytes: int, device="cuda", operands: bool = True):
         import torch
         total_w = sum(sizes.values())
         self.arena = torch.empty(max(1, budget_bytes // 8), dtype=torch.int64, device=device)
         base = self.arena.data_ptr()
+        self.operands = operands
         self.free = {}
         self.top = {}
         self.slot_limbs = {}
+        self.part_limbs = {}
         off = 0
         for n, w in sorted(sizes.items()):
-            L = (gf2x.limbs(n) + 1) // 2 * 2           # 16-byte aligned slots
+            P = (gf2x.limbs(n) + 1) // 2 * 2           # 16-byte aligned parts
+            L = 3 * P if operands else P
             share = int(budget_bytes * w / total_w) // (8 * L)
             self.slot_limbs[n] = L
+            self.part_limbs[n] = P
             self.free[n] = base + 8 * (off + L * np.arange(share, dtype=np.int64))
             self.top[n] = share
             off += share * L
@@ -99,6 +113,14 @@ class SlotPool:
         empty = [n for n, c in self.capacity.items() if c == 0]
         if empty:   # requests of such a size could never be admitted
             raise ValueError(f"budget too small: no output slot for sizes {empty}")
+
+    def result_addr(self, n: int, slot):
+        """Address of the result part of slot(s) of size n."""
+        return slot + (16 * self.part_limbs[n] if self.operands else 0)
+
+    def operand_addrs(self, n: int, slot):
+        """Addresses of the a and b parts of slot(s) of size n (operands=True)."""
+        return slot, slot + 8 * self.part_limbs[n]
 
     def available(self, n: int) -> int:
         return self.top.get(n, 0)
@@ -156,10 +178,16 @@ class Server:
         self.nstreams = streams
         self.use_graphs = use_graphs
         ctx.prepare(sorted(size_weights))
-        self.pool = SlotPool(size_weights, budget_bytes)
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
         self.items_host = [torch.zeros((max_batch, 4), dtype=torch.int64).pin_memory() for _ in range(streams)]
         self.items_dev = [torch.zeros((max_batch, 4), dtype=torch.int64, device="cuda") for _ in range(streams)]
+        # two row copies (a, b) per request into its slot
+        self.rows_host = [torch.zeros((2 * max_batch, 3), dtype=torch.int64).pin_memory() for _ in range(streams)]
+        self.rows_dev = [torch.zeros((2 * max_batch, 3), dtype=torch.int64, device="cuda") for _ in range(streams)]
+        fixed = streams * max_batch * (4 + 6) * 8         # item and copy lists on the device
+        if budget_bytes <= fixed:
+            raise ValueError("budget smaller than the server's item and copy lists")
+        self.pool = SlotPool(size_weights, budget_bytes - fixed)
         self.buckets = []
         b = min_bucket
         while b < max_batch:
@@ -172,13 +200,17 @@ class Server:
 
     def _launch(self, s: int, count: int):
         torch = self.torch
+        st = torch.cuda.current_stream()
+        self.rows_dev[s][:2 * count].copy_(self.rows_host[s][:2 * count], non_blocking=True)
         self.items_dev[s][:count].copy_(self.items_host[s][:count], non_blocking=True)
-        self.ctx.mul_batched_device(self.items_dev[s], count, persistent=True, stream=torch.cuda.current_stream())
+        self.ctx.copy_rows(self.rows_dev[s], 2 * count, stream=st)     # operands into their slots
+        self.ctx.mul_batched_device(self.items_dev[s], count, persistent=True, stream=st, dynamic=True)
 
     def _capture(self):
         torch = self.torch
         for s in range(self.nstreams):
             self.items_host[s].zero_()          # empty slots: nothing to compute while capturing
+            self.rows_host[s].zero_()
             with torch.cuda.stream(self.streams[s]):
                 self._launch(s, self.buckets[0])  # warm-up outside capture
             torch.cuda.synchronize()
@@ -224,9 +256,12 @@ class Server:
             while inflight and inflight[0][1].query():
                 s, ev, rs, addrs = inflight.popleft()
                 done_t[rs] = time.perf_counter() - t0
-                if collect is not None:
-                    collect(rs, addrs, reqs.sizes[rs])
                 szs = reqs.sizes[rs]
+                if collect is not None:
+                    res_addrs = np.empty_like(addrs)
+                    for n in np.unique(szs):
+                        res_addrs[szs == n] = self.pool.result_addr(int(n), addrs[szs == n])
+                    collect(rs, res_addrs, szs)
                 for n in np.unique(szs):
                     self.pool.give_many(int(n), addrs[szs == n])
                 completed += len(rs)
@@ -259,10 +294,23 @@ class Server:
                 s = free_streams.popleft()
                 pa, pb = reqs.ptrs(rs)
                 B = self._bucket(k) if self.use_graphs else k
+                sa = np.empty(k, dtype=np.int64)
+                sb = np.empty(k, dtype=np.int64)
+                sr = np.empty(k, dtype=np.int64)
+                limbs = np.empty(k, dtype=np.int64)
+                for n in np.unique(szs):
+                    sel = szs == n
+                    sa[sel], sb[sel] = self.pool.operand_addrs(int(n), addrs[sel])
+                    sr[sel] = self.pool.result_addr(int(n), addrs[sel])
+                    limbs[sel] = gf2x.limbs(int(n))
+                c = self.rows_host[s].numpy()
+                c[0:2 * k:2, 0], c[0:2 * k:2, 1], c[0:2 * k:2, 2] = pa, sa, limbs
+                c[1:2 * k:2, 0], c[1:2 * k:2, 1], c[1:2 * k:2, 2] = pb, sb, limbs
+                c[2 * k:2 * B] = 0
                 h = self.items_host[s].numpy()
-                h[:k, 0] = pa
-                h[:k, 1] = pb
-                h[:k, 2] = addrs
+                h[:k, 0] = sa
+                h[:k, 1] = sb
+                h[:k, 2] = sr
                 h[:k, 3] = szs | (1 << 32)      # n | GF2X_REDUCE << 32
                 h[k:B] = 0
                 with torch.cuda.stream(self.streams[s]):
@@ -299,7 +347,10 @@ class SizeAwareServer:
         self.torch = torch
         self.sizes = sorted(plans)
         self.max_batch = max_batch
-        self.pool = SlotPool({n: 1 for n in self.sizes}, budget_bytes)
+        fixed = len(self.sizes) * streams_per_size * max_batch * (4 + 6) * 8   # item and copy lists
+        if budget_bytes <= fixed:
+            raise ValueError("budget smaller than the server's item and copy lists")
+        self.pool = SlotPool({n: 1 for n in self.sizes}, budget_bytes - fixed)
         self.ctx = {}
         for n in self.sizes:
             c = gf2x.Context(device, plan_db=None)
@@ -310,6 +361,8 @@ class SizeAwareServer:
         self.items_host = {(n, s): torch.zeros((max_batch, 4), dtype=torch.int64).pin_memory()
                            for n in self.sizes for s in range(streams_per_size)}
         self.items_dev = {k: torch.zeros((max_batch, 4), dtype=torch.int64, device="cuda") for k in self.items_host}
+        self.rows_host = {k: torch.zeros((2 * max_batch, 3), dtype=torch.int64).pin_memory() for k in self.items_host}
+        self.rows_dev = {k: torch.zeros((2 * max_batch, 3), dtype=torch.int64, device="cuda") for k in self.items_host}
         self.buckets = []
         b = min_bucket
         while b < max_batch:
@@ -319,6 +372,7 @@ class SizeAwareServer:
         self.graphs = {}
         for (n, s), host in self.items_host.items():
             host.zero_()
+            self.rows_host[(n, s)].zero_()
             st = self.streams[n][s]
             with torch.cuda.stream(st):
                 self._launch(n, s, self.buckets[0])
@@ -339,9 +393,11 @@ class SizeAwareServer:
 
     def _launch(self, n: int, s: int, count: int):
         torch = self.torch
+        st = torch.cuda.current_stream()
+        self.rows_dev[(n, s)][:2 * count].copy_(self.rows_host[(n, s)][:2 * count], non_blocking=True)
         self.items_dev[(n, s)][:count].copy_(self.items_host[(n, s)][:count], non_blocking=True)
-        self.ctx[n].mul_batched_device(self.items_dev[(n, s)], count, persistent=True,
-                                       stream=torch.cuda.current_stream())
+        self.ctx[n].copy_rows(self.rows_dev[(n, s)], 2 * count, stream=st)     # operands into their slots
+        self.ctx[n].mul_batched_device(self.items_dev[(n, s)], count, persistent=True, stream=st)
 
     def _bucket(self, k: int) -> int:
         for b in self.buckets:
@@ -380,7 +436,7 @@ class SizeAwareServer:
                     if ev.query():
                         done_t[rs] = time.perf_counter() - t0
                         if collect is not None:
-                            collect(rs, addrs, reqs.sizes[rs])
+                            collect(rs, self.pool.result_addr(n, addrs), reqs.sizes[rs])
                         self.pool.give_many(n, addrs)
                         completed += len(rs)
                         free[n].append(s)
@@ -403,10 +459,16 @@ class SizeAwareServer:
                     s = free[n].popleft()
                     pa, pb = reqs.ptrs_of_size(n, rs)
                     B = self._bucket(k)
+                    sa, sb = self.pool.operand_addrs(n, addrs)
+                    L = gf2x.limbs(n)
+                    c = self.rows_host[(n, s)].numpy()
+                    c[0:2 * k:2, 0], c[0:2 * k:2, 1], c[0:2 * k:2, 2] = pa, sa, L
+                    c[1:2 * k:2, 0], c[1:2 * k:2, 1], c[1:2 * k:2, 2] = pb, sb, L
+                    c[2 * k:2 * B] = 0
                     h = self.items_host[(n, s)].numpy()
-                    h[:k, 0] = pa
-                    h[:k, 1] = pb
-                    h[:k, 2] = addrs
+                    h[:k, 0] = sa
+                    h[:k, 1] = sb
+                    h[:k, 2] = self.pool.result_addr(n, addrs)
                     h[:k, 3] = n | (1 << 32)
                     h[k:B] = 0
                     st = self.streams[n][s]
@@ -460,9 +522,10 @@ def serve_plain(ctx: gf2x.Context, reqs: RequestSet, arrivals: np.ndarray, pool:
         while inflight and inflight[0][0].query():
             ev, r, ad = inflight.popleft()
             done_t[r] = time.perf_counter() - t0
+            n = int(reqs.sizes[r])
             if collect is not None:
-                collect(np.array([r]), np.array([ad]), reqs.sizes[[r]])
-            pool.give(int(reqs.sizes[r]), ad)
+                collect(np.array([r]), np.array([pool.result_addr(n, ad)]), reqs.sizes[[r]])
+            pool.give(n, ad)
             completed += 1
             progressed = True
         while pending:
@@ -475,7 +538,16 @@ def serve_plain(ctx: gf2x.Context, reqs: RequestSet, arrivals: np.ndarray, pool:
             pending.popleft()
             pa, pb = reqs.ptrs(np.array([r]))
             s = ss[launches % streams]
-            st = L.gf2x_mulmod_xn1(ctx._h, int(ad), int(pa[0]), int(pb[0]), n, gf2x.ctypes.c_void_p(s.cuda_stream))
+            ra = pool.result_addr(n, ad)
+            if pool.operands:   # the operands into the request's slot (two device-to-device copies)
+                i = int(reqs.index[r])
+                off, P = (ad - pool.arena.data_ptr()) // 8, pool.part_limbs[n]
+                Ln = gf2x.limbs(n)
+                with torch.cuda.stream(s):
+                    pool.arena[off: off + Ln].copy_(reqs.a[n][i], non_blocking=True)
+                    pool.arena[off + P: off + P + Ln].copy_(reqs.b[n][i], non_blocking=True)
+                pa, pb = pool.operand_addrs(n, np.array([ad]))
+            st = L.gf2x_mulmod_xn1(ctx._h, int(ra), int(pa[0]), int(pb[0]), n, gf2x.ctypes.c_void_p(s.cuda_stream))
             if st:
                 raise gf2x.Gf2xError(st, "gf2x_mulmod_xn1")
             ev = torch.cuda.Event()
@@ -492,7 +564,8 @@ def serve_plain(ctx: gf2x.Context, reqs: RequestSet, arrivals: np.ndarray, pool:
     return ServeResult(done_t - arrivals, wall, completed, launches, 1.0, 0, waits)
 
 
-def default_budget(sizes, fraction_inflight: int) -> int:
-    """Bytes for `fraction_inflight` output slots of the average size."""
+def default_budget(sizes, fraction_inflight: int, max_batch: int = 256, streams: int = 3) -> int:
+    """Bytes for `fraction_inflight` request slots (two operands and a result)
+    of the average size, plus the item and copy lists of a Server."""
     avg = sum(gf2x.limbs(n) for n in sizes) / len(sizes)
-    return int(math.ceil(fraction_inflight * avg * 8))
+    return int(math.ceil(fraction_inflight * avg * 8 * 3)) + streams * max_batch * (4 + 6) * 8
