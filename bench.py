@@ -1003,7 +1003,7 @@ def run_c5(device, requests):
     out["tight_budget_4MiB_load_0.95"] = dict(r.summary(), offered_per_s=0.95 * cap,
                                             slots=sum(tight.pool.capacity.values()))
     ctx.sync_status()
-    # plain per-request launches (each copies its operands into its slot, then one launch), every request
+    # plain per-request launches (one launch each, holding a request slot), every request
     m = len(sizes)
     sub_reqs = serve.RequestSet(reqs.sizes[:m], reqs.index[:m], reqs.a, reqs.b)
     pool = serve.SlotPool(weights, budget)

@@ -495,7 +495,8 @@ class SizeAwareServer:
 
 def serve_plain(ctx: gf2x.Context, reqs: RequestSet, arrivals: np.ndarray, pool: SlotPool, streams: int = 3,
                 collect=None) -> ServeResult:
-    """Baseline: one launch (one CTA) per request on arrival, round-robin over streams."""
+    """Baseline: one launch (one CTA) per request on arrival, round-robin over
+    streams; each request holds a whole slot of the budget while in flight."""
     import torch
     N = len(reqs)
     unknown = set(np.unique(reqs.sizes).tolist()) - set(pool.capacity)
@@ -538,15 +539,11 @@ def serve_plain(ctx: gf2x.Context, reqs: RequestSet, arrivals: np.ndarray, pool:
             pending.popleft()
             pa, pb = reqs.ptrs(np.array([r]))
             s = ss[launches % streams]
+            # the request's slot is reserved whole (operands and result), but the
+            # one launch reads the operands where they are: copying them in would
+            # cost this baseline two more host calls per request (the batched
+            # servers copy a whole batch in one captured launch)
             ra = pool.result_addr(n, ad)
-            if pool.operands:   # the operands into the request's slot (two device-to-device copies)
-                i = int(reqs.index[r])
-                off, P = (ad - pool.arena.data_ptr()) // 8, pool.part_limbs[n]
-                Ln = gf2x.limbs(n)
-                with torch.cuda.stream(s):
-                    pool.arena[off: off + Ln].copy_(reqs.a[n][i], non_blocking=True)
-                    pool.arena[off + P: off + P + Ln].copy_(reqs.b[n][i], non_blocking=True)
-                pa, pb = pool.operand_addrs(n, np.array([ad]))
             st = L.gf2x_mulmod_xn1(ctx._h, int(ra), int(pa[0]), int(pb[0]), n, gf2x.ctypes.c_void_p(s.cuda_stream))
             if st:
                 raise gf2x.Gf2xError(st, "gf2x_mulmod_xn1")

@@ -49,3 +49,26 @@ def test_slot_pool_rejects_a_budget_without_a_slot_for_some_size():
     import pytest
     with pytest.raises(ValueError):
         serve.SlotPool({12323: 1, 57637: 1}, 8000, device="cpu")   # 4000 bytes each: no 57637 slot
+
+
+def test_request_slots_hold_both_operands_and_the_result():
+    """A request slot holds a, b and r (each part 16-byte aligned), so the
+    budget admits a third of the requests a results-only pool would."""
+    sizes = {17669: 1, 57637: 1}
+    budget = 6 << 20
+    full = serve.SlotPool(sizes, budget, device="cpu")
+    res_only = serve.SlotPool(sizes, budget, device="cpu", operands=False)
+    for n in sizes:
+        P = full.part_limbs[n]
+        assert P >= gf2x.limbs(n) and P % 2 == 0 and full.slot_limbs[n] == 3 * P
+        assert abs(full.capacity[n] * 3 - res_only.capacity[n]) <= 3
+        ad = int(full.free[n][0])
+        a, b = full.operand_addrs(n, ad)
+        assert (a, b, full.result_addr(n, ad)) == (ad, ad + 8 * P, ad + 16 * P)
+        assert res_only.result_addr(n, ad) == ad
+
+
+def test_server_budget_must_cover_its_lists():
+    import pytest
+    # the item and copy lists of 3 streams x 2048 items take 480 KiB of the budget
+    assert serve.default_budget([17669], 0, max_batch=2048, streams=3) == 3 * 2048 * 80
