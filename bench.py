@@ -329,6 +329,16 @@ def run_ours(args, w):
         except ImportError:
             import_oracle_ok = False
 
+    # the spot check left the GPU idle: untimed steps for ~0.2 s bring the
+    # clocks back up before the timed region
+    t_ramp = time.perf_counter()
+    i_ramp = 0
+    while time.perf_counter() - t_ramp < 0.2:
+        for _ in range(8):
+            step(i_ramp)
+            i_ramp += 1
+        torch.cuda.synchronize()
+
     # ---- timed region: K steps, per-launch events on the launching stream
     K = args.steps
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]

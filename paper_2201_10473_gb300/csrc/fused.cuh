@@ -180,19 +180,46 @@ __device__ __forceinline__ void leaf_pass(const GPlan &P, uint32_t *base, uint32
 
 // ---------------------------------------------------------------- staging
 // Words 0..T0-1 of an operand: the caller's ceil(n/64) limbs read as 32-bit
-// words, bits >= n cleared, zero padding up to the plan size.
+// words, bits >= n cleared, zero padding up to the plan size.  A row that
+// starts on a 16-byte boundary is read with 128-bit loads (four words per
+// thread), any other (8-byte aligned) row with 64-bit loads; the choice
+// depends on the address only.  Loads stay inside the row's ceil(n/64) limbs.
+__device__ __forceinline__ uint32_t stage_word(uint32_t v, uint32_t w, uint32_t L32, uint32_t r)
+{
+    v = w < L32 ? v : 0u;
+    return (w == L32 - 1 && r) ? (v & ((1u << r) - 1u)) : v;
+}
+
 __device__ __forceinline__ void stage_operand(uint32_t *dst, const uint64_t *src, const GPlan &P)
 {
-    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
-    const uint32_t L32 = P.L32, T0 = P.T0, r = P.n & 31u;
-    for (uint32_t w = threadIdx.x; w < T0; w += blockDim.x) {
-        uint32_t v = 0u;
-        if (w < L32) {
-            v = __ldg(s32 + w);
-            if (w == L32 - 1 && r)
-                v &= (1u << r) - 1u;
+    const uint32_t L32 = P.L32, T0 = P.T0, r = P.n & 31u, W = 2u * P.L64;   // W: words in the row
+    if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        for (uint32_t q = threadIdx.x; 4u * q < T0; q += blockDim.x) {
+            const uint32_t w = 4u * q;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (w + 3u < W) {
+                v = __ldg(s4 + q);
+            } else if (w < W) {   // the row's last words (W is even)
+                const uint2 h = __ldg(reinterpret_cast<const uint2 *>(src) + 2u * q);
+                v.x = h.x;
+                v.y = h.y;
+            }
+            const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k)
+                if (w + k < T0)
+                    dst[w + k] = stage_word(vv[k], w + k, L32, r);
         }
-        dst[w] = v;
+    } else {
+        const uint2 *s2 = reinterpret_cast<const uint2 *>(src);
+        for (uint32_t q = threadIdx.x; 2u * q < T0; q += blockDim.x) {
+            const uint32_t w = 2u * q;
+            const uint2 v = w < W ? __ldg(s2 + q) : make_uint2(0u, 0u);
+            dst[w] = stage_word(v.x, w, L32, r);
+            if (w + 1u < T0)
+                dst[w + 1u] = stage_word(v.y, w + 1u, L32, r);
+        }
     }
 }
 
@@ -570,29 +597,34 @@ __device__ __forceinline__ void interp_level(const GPlan &P, const GLevel &L, co
 // Full product: the first ceil((2n-1)/64) limbs.  Reduced product:
 // r = (c mod X^n) + (c >> n), since X^n = 1 in F2[X]/(X^n - 1) and deg c <= 2n-2
 // (Sec. 1, circulant isomorphism).
+__device__ __forceinline__ uint32_t fold_word(const GPlan &P, const uint32_t *C, uint32_t q, uint32_t twoT)
+{
+    const uint32_t sh = P.n >> 5, s = P.n & 31u, L32 = P.L32;
+    const uint32_t lo = q < twoT ? C[q] : 0u;
+    const uint32_t i0 = q + sh;
+    const uint32_t h0 = i0 < twoT ? C[i0] : 0u;
+    const uint32_t h1 = i0 + 1u < twoT ? C[i0 + 1u] : 0u;
+    uint32_t v = lo ^ __funnelshift_r(h0, h1, s);
+    if (q >= L32)
+        v = 0u;
+    else if (q == L32 - 1 && s)
+        v &= (1u << s) - 1u;
+    return v;
+}
+
+// Results leave as whole 64-bit limbs (one 8-byte store per limb).
 __device__ __forceinline__ void epilogue(const GPlan &P, const DevItem &it, const uint32_t *C, uint32_t *err)
 {
-    uint32_t *o32 = reinterpret_cast<uint32_t *>(it.out);
+    uint2 *o2 = reinterpret_cast<uint2 *>(it.out);
     const uint32_t twoT = 2u * P.T0;
     if (it.flags & 1u) {
-        const uint32_t nw = 2u * P.L64, sh = P.n >> 5, s = P.n & 31u, L32 = P.L32;
-        for (uint32_t q = threadIdx.x; q < nw; q += blockDim.x) {
-            const uint32_t lo = q < twoT ? C[q] : 0u;
-            const uint32_t i0 = q + sh;
-            const uint32_t h0 = i0 < twoT ? C[i0] : 0u;
-            const uint32_t h1 = i0 + 1u < twoT ? C[i0 + 1u] : 0u;
-            const uint32_t f = __funnelshift_r(h0, h1, s);
-            uint32_t v = lo ^ f;
-            if (q >= L32)
-                v = 0u;
-            else if (q == L32 - 1 && s)
-                v &= (1u << s) - 1u;
-            o32[q] = v;
-        }
+        for (uint32_t l = threadIdx.x; l < P.L64; l += blockDim.x)
+            o2[l] = make_uint2(fold_word(P, C, 2u * l, twoT), fold_word(P, C, 2u * l + 1u, twoT));
     } else {
-        const uint32_t nw = 2u * P.Lfull64;
-        for (uint32_t q = threadIdx.x; q < nw; q += blockDim.x)
-            o32[q] = q < twoT ? C[q] : 0u;
+        for (uint32_t l = threadIdx.x; l < P.Lfull64; l += blockDim.x) {
+            const uint32_t q = 2u * l;
+            o2[l] = make_uint2(q < twoT ? C[q] : 0u, q + 1u < twoT ? C[q + 1u] : 0u);
+        }
     }
     if (P.checked) {
         const uint32_t top = 2u * P.n - 1u;  // first bit that must be zero
