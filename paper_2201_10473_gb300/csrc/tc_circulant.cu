@@ -16,7 +16,7 @@
 // p0, p0 - 32, p0 - 64, ... (mod n): row q then starts exactly 16 bytes (32
 // fp4 elements) after row q - 1 in ONE nibble sequence R[t] = a[(p0 - t) mod
 // n], so a shared-memory descriptor with a 16-byte leading and a 128-byte
-// stride offset reads the whole 240 x 64 operand tile out of R.  For odd n
+// stride offset reads the whole 224 x 64 operand tile out of R.  For odd n
 // the stride -32 mod n visits every position once, so the positions are
 // enumerated as q = 0, 1, 2, ... with p(q) = (n - 1 - 32 q) mod n.
 //
@@ -26,12 +26,14 @@
 //                     one 4 KB chunk per tile of 128 rows and K-step of 64;
 //  tc_gemm_kernel     persistent, one CTA per SM: a bulk-copy producer
 //                     thread, an MMA thread, four epilogue warps reading the
-//                     counts from TMEM; each unit is 128 products x 480
-//                     positions over all n inputs; the parities go out in
-//                     position-index (q) order;
+//                     counts from TMEM; each unit is 128 products x 224
+//                     positions over all n inputs, and TMEM holds two
+//                     accumulator buffers, so a unit's parities are read
+//                     while the next unit accumulates; the parities go out
+//                     in position-index (q) order;
 //  tc_assemble_kernel q order -> bit order: r_j[p] = parity[j][q(p)], a
 //                     funnel-shift gather of each bit column and a warp
-//                     ballot transpose per 32 output words.
+//                     butterfly transpose per 32 output words.
 // Constant time: every loop bound, address and branch depends on n, count
 // and thread indices only; operand bits flow through data paths.
 // Every wait on a barrier is bounded (globaltimer); on a timeout the CTA
@@ -49,13 +51,13 @@ namespace gf2x {
 namespace {
 
 constexpr uint32_t kTcThreads = 256;          // warps: 0 producer, 1 MMA, 2-3 idle, 4-7 epilogue
-constexpr uint32_t kKS = 4;                   // K-steps (of 64 inputs) per ring stage
-constexpr uint32_t kRing = 8;                 // A stages
+constexpr uint32_t kKS = 8;                   // K-steps (of 64 inputs) per ring stage
+constexpr uint32_t kRing = 4;                 // A stages
 constexpr uint32_t kChunk = 4096;             // bytes of one K-step of A: 128 rows x 64 fp4
 constexpr uint32_t kStage = kKS * kChunk;
-constexpr uint32_t kNT = 240;                 // N of one MMA
-constexpr uint32_t kNU = 2 * kNT;             // positions per unit
-constexpr uint32_t kSfCol = kNU;              // TMEM columns kNU..511 hold the scale factors (all 1.0)
+constexpr uint32_t kNT = 224;                 // N of one MMA = positions per unit (7 words of parities)
+constexpr uint32_t kNU = kNT;
+constexpr uint32_t kSfCol = 2 * kNT;          // TMEM: two accumulator buffers, then the scale factors (all 1.0)
 constexpr uint32_t kRWinMax = 16 * (kNU - 1) + 32 * (kTcMaxN / 64);   // bytes of an R window
 constexpr uint32_t kROff = kRing * kStage;
 constexpr uint32_t kRBytes = (kRWinMax + 127) / 128 * 128;
@@ -234,15 +236,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const TcGemmArgs
     extern __shared__ __align__(1024) uint8_t sm[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const uint32_t sbase = su32(sm);
-    // barriers: full[kRing], empty[kRing], rfull[2], rempty[2], done, tfree
+    // barriers: full[kRing], empty[kRing], rfull[2], rempty[2], done[2], tfree[2], drain
+    // (done / tfree per TMEM accumulator buffer: unit k uses buffer k & 1)
     const uint32_t bar0 = sbase + kBarOff;
     auto full = [&](uint32_t i) { return bar0 + 8u * i; };
     auto empty = [&](uint32_t i) { return bar0 + 8u * (kRing + i); };
     auto rfull = [&](uint32_t i) { return bar0 + 8u * (2 * kRing + i); };
     auto rempty = [&](uint32_t i) { return bar0 + 8u * (2 * kRing + 2 + i); };
-    const uint32_t done = bar0 + 8u * (2 * kRing + 4), tfree = bar0 + 8u * (2 * kRing + 5);
-    const uint32_t drain = bar0 + 8u * (2 * kRing + 6);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kBarOff + 8u * (2 * kRing + 8));
+    auto done = [&](uint32_t i) { return bar0 + 8u * (2 * kRing + 4 + i); };
+    auto tfree = [&](uint32_t i) { return bar0 + 8u * (2 * kRing + 6 + i); };
+    const uint32_t drain = bar0 + 8u * (2 * kRing + 8);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kBarOff + 8u * (2 * kRing + 10));
     volatile uint32_t *abort_flag = tslot + 1;
 
     if (threadIdx.x == 0) {
@@ -253,9 +257,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const TcGemmArgs
         for (uint32_t i = 0; i < 2; ++i) {
             mbar_init(rfull(i), 1);
             mbar_init(rempty(i), 1);
+            mbar_init(done(i), 1);
+            mbar_init(tfree(i), 4);   // one arrival per epilogue warp
         }
-        mbar_init(done, 1);
-        mbar_init(tfree, 4);   // one arrival per epilogue warp
         mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -314,14 +318,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const TcGemmArgs
         uint32_t g = 0, k = 0;
         bool issued = false;
         for (uint32_t u = blockIdx.x; u < args.units && !failed; u += gridDim.x, ++k) {
-            const uint32_t rb = k & 1u;
+            const uint32_t rb = k & 1u, tb = k & 1u;
+            // buffer tb was last read by the epilogue of unit k - 2
             if (!mbar_wait(rfull(rb), (k >> 1) & 1u, abort_flag) ||
-                (k >= 1 && !mbar_wait(tfree, (k - 1u) & 1u, abort_flag))) {
+                (k >= 2 && !mbar_wait(tfree(tb), ((k >> 1) - 1u) & 1u, abort_flag))) {
                 failed = true;
                 break;
             }
             fence_after();
-            const uint32_t rwin = sbase + kROff + rb * kRBytes;
+            const uint32_t rwin = sbase + kROff + rb * kRBytes, d = tmem + tb * kNT;
             for (uint32_t s0 = 0; s0 < S; s0 += kKS, ++g) {
                 const uint32_t slot = g % kRing, ks = min(kKS, S - s0);
                 if (!mbar_wait(full(slot), (g / kRing) & 1u, abort_flag)) {
@@ -331,10 +336,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const TcGemmArgs
                 fence_after();
                 for (uint32_t i = 0; i < ks; ++i) {
                     const uint32_t s = s0 + i;
-                    const uint64_t adesc = sdesc(sbase + slot * kStage + i * kChunk, 128, 256);
-                    mma_fp4(tmem, adesc, sdesc(rwin + 32u * s, 16, 128), tmem + kSfCol, tmem + kSfCol + 16, s > 0);
-                    mma_fp4(tmem + kNT, adesc, sdesc(rwin + 16u * kNT + 32u * s, 16, 128), tmem + kSfCol,
-                            tmem + kSfCol + 16, s > 0);
+                    mma_fp4(d, sdesc(sbase + slot * kStage + i * kChunk, 128, 256), sdesc(rwin + 32u * s, 16, 128),
+                            tmem + kSfCol, tmem + kSfCol + 16, s > 0);
                 }
                 issued = true;
                 mma_commit(empty(slot));   // the stage is free once these MMAs have read it
@@ -342,7 +345,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const TcGemmArgs
             if (failed)
                 break;
             mma_commit(rempty(rb));
-            mma_commit(done);
+            mma_commit(done(tb));
         }
         if (failed) {
             *abort_flag = 1;
@@ -354,12 +357,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const TcGemmArgs
             }
         }
     } else if (warp >= 4) {
-        // ---- epilogue: counts -> parities, 480 positions of 32 products per warp
+        // ---- epilogue: counts -> parities, 224 positions of 32 products per warp
         const uint32_t wq = warp & 3u;
         uint32_t k = 0;
         for (uint32_t u = blockIdx.x; u < args.units; u += gridDim.x, ++k) {
-            const uint32_t tile = u / args.V, v = u - tile * args.V;
-            const bool ok = mbar_wait(done, k & 1u, abort_flag, 256);
+            const uint32_t tile = u / args.V, v = u - tile * args.V, tb = k & 1u;
+            const bool ok = mbar_wait(done(tb), (k >> 1) & 1u, abort_flag, 256);
             if (!__all_sync(0xffffffffu, ok)) {   // warp-uniform: the loads below are warp-synchronous
                 failed = true;
                 break;
@@ -378,7 +381,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const TcGemmArgs
                       "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
                       "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
                       "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(tmem + ((wq * 32u) << 16) + c));
+                    : "r"(tmem + ((wq * 32u) << 16) + tb * kNT + c));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 uint32_t word = 0;
 #pragma unroll
@@ -390,7 +393,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const TcGemmArgs
             fence_before();
             __syncwarp();
             if (lane == 0)
-                mbar_arrive(tfree);
+                mbar_arrive(tfree(tb));
         }
         if (failed)
             *abort_flag = 1;
