@@ -73,3 +73,63 @@ def test_launch_time_independent_of_operand_bits(n):
         assert spread < 1.05, ms
     finally:
         ctx.close()
+
+
+def _median_tc_ms(ctx, da, db, n, out, reps=7, inner=10):
+    for _ in range(3):
+        ctx.mulmod_shared_tc(da, db, n, out=out)
+    times = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(inner):
+            ctx.mulmod_shared_tc(da, db, n, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / inner)
+    return float(np.median(times))
+
+
+def test_tensor_core_call_time_independent_of_operand_bits():
+    """The shared-operand GEMM on the tensor cores: the same launches for a
+    dense, an all-zero, an all-ones and a sparse (HQC-128 weight 75) b, and
+    a dense or all-ones a; times agree within a few percent, results stay
+    bit-exact."""
+    from paper_2201_10473_gb300 import Context
+    ctx = Context(0)
+    try:
+        n, count = 17669, 2048
+        L = wl.limbs(n)
+        a_dense = wl.dense_operands(6100, n, 1, 0)[0]
+        a_ones = wl.mask_top(np.full((1, L), np.uint64(0xFFFFFFFFFFFFFFFF)), n)[0]
+        b_dense = wl.dense_operands(6100, n, count, 1)
+        classes = {
+            "dense": (a_dense, b_dense),
+            "zero_b": (a_dense, np.zeros((count, L), np.uint64)),
+            "ones_b": (a_dense, wl.mask_top(np.full((count, L), np.uint64(0xFFFFFFFFFFFFFFFF)), n)),
+            "sparse75_b": (a_dense, wl.sparse_operands(6101, n, 75, count)),
+            "ones_a": (a_ones, b_dense),
+        }
+        out = torch.empty((count, L), dtype=torch.int64, device="cuda")
+        dev = {name: (to_dev(a), to_dev(b)) for name, (a, b) in classes.items()}
+        sample = np.arange(0, count, 512)
+        for name, (da, db) in dev.items():
+            ctx.mulmod_shared_tc(da, db, n, out=out)
+            a, b = classes[name]
+            exp = oracle.mul_batch(np.repeat(a[None], len(sample), 0), b[sample], n, reduce=True)
+            assert np.array_equal(to_host(out)[sample], exp), name
+        da, db = dev["dense"]
+        t_end = time.time() + 1.0
+        while time.time() < t_end:
+            ctx.mulmod_shared_tc(da, db, n, out=out)
+            torch.cuda.synchronize()
+        rounds = {name: [] for name in dev}
+        for _ in range(3):
+            for name, (da, db) in dev.items():
+                rounds[name].append(_median_tc_ms(ctx, da, db, n, out))
+        ms = {name: min(t) for name, t in rounds.items()}
+        ctx.sync_status()
+        assert max(ms.values()) / min(ms.values()) < 1.05, ms
+    finally:
+        ctx.close()
