@@ -51,8 +51,17 @@ namespace gf2x {
 namespace {
 
 constexpr uint32_t kTcThreads = 256;          // warps: 0 producer, 1 MMA, 2-3 idle, 4-7 epilogue
-constexpr uint32_t kKS = 8;                   // K-steps (of 64 inputs) per ring stage
-constexpr uint32_t kRing = 4;                 // A stages
+// Pipeline shape (compile-time): the MMAs per barrier wait and commit are
+// what counts -- measured at 4096 x 17669: 2 K-steps per stage 6.0 M/s, 4:
+// 8.4, 8: 12.8, 16: 13.0 -- while the ring depth barely matters.
+#ifndef GF2X_TC_KS
+#define GF2X_TC_KS 16
+#endif
+#ifndef GF2X_TC_RING
+#define GF2X_TC_RING 2
+#endif
+constexpr uint32_t kKS = GF2X_TC_KS;          // K-steps (of 64 inputs) per ring stage
+constexpr uint32_t kRing = GF2X_TC_RING;      // A stages
 constexpr uint32_t kChunk = 4096;             // bytes of one K-step of A: 128 rows x 64 fp4
 constexpr uint32_t kStage = kKS * kChunk;
 constexpr uint32_t kNT = 224;                 // N of one MMA = positions per unit (7 words of parities)
@@ -101,6 +110,8 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
 }
 
+// One test of a barrier phase (try_wait may suspend the thread briefly when
+// the phase is not complete yet; a non-suspending test_wait measured the same).
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
