@@ -615,7 +615,7 @@ def run_c3(device):
     from paper_2201_10473_gb300 import costmodel
     measured_sets = autotune.mixed_plan_sets(log, weights, 2048, top=3)
     model = costmodel.CostModel(seed=0)
-    model.fit(log, steps=3000, seed=0)
+    model.fit(costmodel.training_records(log), steps=3000, seed=0)
     model_sets = autotune.model_mixed_plan_sets(model, weights, 2048, top=6)
     timed = []
     for origin, sets in (("log", measured_sets), ("model", model_sets)):

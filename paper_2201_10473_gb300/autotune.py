@@ -376,7 +376,7 @@ def main(argv=None):
     if a.guided:
         from . import costmodel
         model = costmodel.CostModel(seed=a.seed)
-        model.fit(packaged_log())
+        model.fit(costmodel.training_records(packaged_log()))
     prior = None
     if a.from_log:
         prior = packaged_log() if a.from_log == "packaged" else read_log(a.from_log)

@@ -95,7 +95,7 @@ def test_learned_model_beats_unguided_search(holdout):
     of the exhaustive best comes far earlier than in random order, and its top
     10 are within 10% of the best (exhaustive search gives the best)."""
     from paper_2201_10473_gb300 import autotune, costmodel
-    r = costmodel.evaluate_gain(autotune.packaged_log(), holdout, 2048, k=10, steps=3000)
+    r = costmodel.evaluate_gain(costmodel.training_records(autotune.packaged_log()), holdout, 2048, k=10, steps=3000)
     assert r["model_measurements_to_5pct"] * 4 <= r["random_expected_measurements_to_5pct"], r
     assert r["regret_top_k"] <= 0.10, r
 
@@ -108,7 +108,7 @@ def test_guided_search_on_an_unseen_size():
     from paper_2201_10473_gb300 import Context, autotune, costmodel
     n, batch = 30011, 2048
     model = costmodel.CostModel(seed=1)
-    model.fit(autotune.packaged_log(), steps=3000)
+    model.fit(costmodel.training_records(autotune.packaged_log()), steps=3000)
     tuner = autotune.Autotuner(Context(0, plan_db=None), None, reps=3, warmup=1)
     try:
         cands = autotune.candidate_specs(n)
