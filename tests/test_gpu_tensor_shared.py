@@ -168,3 +168,37 @@ def test_rejected_arguments():
         assert f(ctx._h, out.data_ptr(), x.data_ptr(), x.data_ptr(), 17669, 4, L - 1, L, None) == 1  # short stride
     finally:
         ctx.close()
+
+
+def test_captured_in_a_cuda_graph_and_replayed_with_new_vectors():
+    """A server with one fixed key captures the call once and replays it
+    with new vectors in the same buffers (the scratch is sized by a first
+    call outside the capture)."""
+    from paper_2201_10473_gb300 import Context
+    n, count = 17669, 300
+    ctx = Context(0)
+    try:
+        a = wl.dense_operands(5700, n, 1, 0)[0]
+        da = to_dev(a)
+        db = to_dev(wl.dense_operands(5700, n, count, 1))
+        out = torch.zeros((count, wl.limbs(n)), dtype=torch.int64, device="cuda")
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            ctx.mulmod_shared_tc(da, db, n, out=out)        # warm-up: scratch and shapes
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            ctx.mulmod_shared_tc(da, db, n, out=out)
+        for rep in range(3):
+            b = wl.dense_operands(5701 + rep, n, count, 1)
+            db.copy_(to_dev(b))
+            out.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            ctx.sync_status()
+            rows = np.array([0, 127, 128, count - 1])
+            assert np.array_equal(to_host(out)[rows], _expect(a, b[rows], n)), rep
+    finally:
+        ctx.close()
