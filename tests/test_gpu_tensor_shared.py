@@ -189,7 +189,7 @@ def test_captured_in_a_cuda_graph_and_replayed_with_new_vectors():
         torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
+        with torch.cuda.graph(g, stream=side):                # the warm-up's stream: no cross-stream scratch wait
             ctx.mulmod_shared_tc(da, db, n, out=out)
         for rep in range(3):
             b = wl.dense_operands(5701 + rep, n, count, 1)
