@@ -492,6 +492,10 @@ def run_ours(args, w):
         "parity_checked": import_oracle_ok,
         "e2e_sample_checked_against_oracle": e2e_ok,
         "workloads": extras,
+        "paper_context": {"note": "the paper's own CPU figures (unreduced product, one core), context only",
+                          "hw": "Intel Core i7-1165G7 (Tiger Lake) 2.8 GHz, Turbo off, one thread",
+                          "hqc128_17669_avx512_cycles": 14872, "hqc128_17669_avx512_mults_per_s": 2.8e9 / 14872,
+                          "hqc256_57637_avx512_cycles": 110568},
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -772,6 +776,16 @@ def run_shared(device):
             rates.setdefault(name, []).append(count / (ms * 1e-3))
         it[0] = 0
         ms_tc.append(_time_calls(call_tc, 40, 3))
+    # the HQC encapsulation shape: the shared key times secret vectors of
+    # weight 75, on the tensor cores and through the constant-time sparse
+    # kernel (positions; the key repeated in every row)
+    sp_rows = wl.sparse_operands(wl.BASE_SEED + 12, n, 75, count)
+    sp_pos = np.stack([np.flatnonzero(np.unpackbits(r.view(np.uint8), bitorder="little"))[:75] for r in sp_rows])
+    dsp, dpos = _dev(sp_rows), torch.from_numpy(sp_pos.astype(np.int32)).cuda()
+    ms_tc_sparse = _time_calls(lambda: ctx.mulmod_shared_tc(dh, dsp, n, out=out), 40, 3)
+    ms_sparse_kernel = _time_calls(lambda: ctx.mulmod_sparse(dhs, dpos, n, out=out), 40, 3)
+    ok_sp = bool(np.array_equal(_host(out)[::512], np.stack([oracle.mulmod(h[0], sp_rows[p], n)
+                                                             for p in range(0, count, 512)])))
     sample = np.arange(0, count, 512)
     exp = np.stack([oracle.mulmod(h[0], vecs[0][p], n) for p in sample])
     it[0] = 0
@@ -801,6 +815,9 @@ def run_shared(device):
     return {"workload": "shared-key-17669-mulmod", "products": count, "plan": plan,
             "shared_mults_per_s": shared, "unshared_mults_per_s": unshared, "shared_over_unshared": shared / unshared,
             "tensor_core_mults_per_s": count / (ms * 1e-3), "tensor_over_shared_comb": count / (ms * 1e-3) / shared,
+            "hqc_encaps_shape_weight75": {"tensor_core_mults_per_s": count / (ms_tc_sparse * 1e-3),
+                                          "sparse_kernel_mults_per_s": count / (ms_sparse_kernel * 1e-3),
+                                          "sample_checked_against_oracle": ok_sp},
             "tensor_core_roofline": {"bound": "tensor", "dtype": "fp4 e2m1 (0/1), fp32 counts", "achieved": achieved,
                                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                                      "peak_note": "MEASURED_PEAKS bf16_tflops x 6 (nominal fp4/bf16); whole call timed",
