@@ -894,7 +894,7 @@ def run_sparse(device):
         ctx = Context(device, batch_hint=count)
         rows = wl.sparse_operands(wl.BASE_SEED + 10, n, w, count)
         pos = np.stack([np.flatnonzero(np.unpackbits(r.view(np.uint8), bitorder="little"))[:w] for r in rows])
-        R = 4
+        R = 16 if n < 40000 else 10     # rotating a sets: more than the 129 MB L2 in all
         da = [_dev(wl.dense_operands(wl.BASE_SEED + 10, n, count, 0, first=r * count)) for r in range(R)]
         dpos, dden = torch.from_numpy(pos.astype(np.int32)).cuda(), _dev(rows)
         out = torch.empty((count, wl.limbs(n)), dtype=torch.int64, device="cuda")

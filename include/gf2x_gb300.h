@@ -328,9 +328,11 @@ gf2x_status gf2x_mul_unbalanced(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a,
  * positions (repeated positions cancel, as in F2); result row p = a_p * b_p
  * mod X^n - 1 in ceil(n/64) limbs, bits above n zero.  Sec. 1 rules out
  * multiplications that use the sparsity through branches or memory
- * addresses; this one never does: each position becomes the masks of a
- * barrel shifter and the count of a funnel shift on the doubled vector
- * a + X^n a, so the work and the addresses depend on n, w and count only.
+ * addresses; this one never does: each position becomes the select masks of
+ * barrel shifters (register renames and fixed-offset lane shuffles, every
+ * stage executed) and the count of a funnel shift on the doubled vector
+ * a + X^n a, so the work, the addresses and the shuffle lanes depend on n,
+ * w and count only.
  *  - a: count rows of ceil(n/64) limbs, stride_a limbs apart (bits above n
  *    ignored); pos: count rows of w uint32 positions, stride_pos entries
  *    apart, each < n (a position >= n gives an unspecified row, never an
@@ -398,17 +400,20 @@ gf2x_status gf2x_mulmod_shared_tc(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a,
                                   size_t count, size_t stride_b, size_t stride_r, gf2x_stream stream);
 
 /* The kernel shape gf2x_mulmod_sparse uses for n (host only, needs no GPU).
- * The warp's cyclic window is 32 x words_per_lane words; the word offset's
- * bits are applied by shared_stages shifts in shared memory (the largest,
- * each >= 256 words) and then register_stages shifts in registers
- * (shared_stages + register_stages = bits of n/32).  GF2X_EUNSUPPORTED for n
- * outside [1, 65536]. */
+ * A warp holds words_per_lane registers of the doubled vector, word
+ * lane + 32 k in register k, and result_words_per_lane accumulator
+ * registers (32 x result_words_per_lane >= ceil(n/32) + 1).  The word offset
+ * of a position is applied by shared_stages shifts in shared memory (its top
+ * bits, each shift >= 256 words), register_stages shifts by whole registers
+ * and lane_stages (5) lane rotations; its bit offset by a funnel shift.
+ * GF2X_EUNSUPPORTED for n outside [1, 65536]. */
 typedef struct {
     uint32_t n;
     uint32_t words_per_lane;
+    uint32_t result_words_per_lane;
     uint32_t shared_stages;
     uint32_t register_stages;
-    uint32_t doubled_in_registers;  /* 1: a + X^n a itself stays in registers */
+    uint32_t lane_stages;
     uint32_t smem_bytes;            /* dynamic shared memory per CTA (four warps) */
 } gf2x_sparse_info;
 

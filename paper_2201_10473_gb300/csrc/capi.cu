@@ -1005,7 +1005,7 @@ extern "C" gf2x_status gf2x_mulmod_sparse(gf2x_ctx *ctx, uint64_t *r, const uint
     args.n = n;
     args.w = w;
     args.count = (uint32_t)count;
-    args.stages = sh.T - sh.pre;
+    args.T = sh.T;
     args.pre = sh.pre;
     args.d_words = sh.d_words;
     args.b_words = sh.b_words;
@@ -1024,9 +1024,13 @@ extern "C" gf2x_status gf2x_sparse_info_get(uint32_t n, gf2x_sparse_info *info)
         return GF2X_EUNSUPPORTED;
     info->n = n;
     info->words_per_lane = sh.C;
+    info->result_words_per_lane = sh.R;
     info->shared_stages = sh.pre;
-    info->register_stages = sh.T - sh.pre;
-    info->doubled_in_registers = sh.staged ? 0u : 1u;
+    uint32_t th = 0;
+    while ((sh.QH >> th) != 0u)
+        ++th;
+    info->register_stages = th;
+    info->lane_stages = 5;
     info->smem_bytes = (uint32_t)sparse_smem_bytes(sh);
     return GF2X_OK;
 }

@@ -37,14 +37,14 @@ struct SparseArgs {
     uint64_t *r;              // result rows, ceil(n/64) limbs, stride_r limbs apart
     size_t stride_a, stride_pos, stride_r;
     uint32_t n, w, count;
-    uint32_t stages;          // barrel stages in registers
-    uint32_t pre;             // largest stages in shared memory first (staged variant)
-    uint32_t d_words, b_words; // shared words per warp: doubled vector, stage buffer
+    uint32_t T;               // bits of the largest word offset n/32
+    uint32_t pre;             // its top bits applied in shared memory first
+    uint32_t d_words, b_words; // shared words: doubled vector, each warp's stage buffer
 };
 struct SparseShape {
     uint32_t N, T;            // words of a, bits of the largest word offset n/32
-    uint32_t C;               // window words per lane
-    uint32_t staged, pre, d_words, b_words;
+    uint32_t R, QH, C;        // result registers per lane, register offsets up to QH, window registers
+    uint32_t pre, d_words, b_words;
 };
 bool sparse_shape(uint32_t n, SparseShape *sh);
 size_t sparse_smem_bytes(const SparseShape &sh);

@@ -167,8 +167,8 @@ def plan_info(n: int, spec: str | None = None) -> dict:
 
 
 class SparseInfo(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_uint32) for f in ("n", "words_per_lane", "shared_stages", "register_stages",
-                                               "doubled_in_registers", "smem_bytes")]
+    _fields_ = [(f, ctypes.c_uint32) for f in ("n", "words_per_lane", "result_words_per_lane", "shared_stages",
+                                               "register_stages", "lane_stages", "smem_bytes")]
 
 
 def sparse_info(n: int) -> dict:

@@ -1,9 +1,9 @@
 """Constant-time sparse x dense products mod X^n - 1 (gf2x_mulmod_sparse):
 every row equals the oracle's product of a and the dense form of the
 position list (repeated positions cancel), and the dense path's product of
-the same operands, bit for bit.  Covers every kernel shape (D in registers
-with 9, 17 and 35 words per lane; the staged kernel with 0, 2 and 4 shared
-stages), positions 0 and n - 1, w = 0, ragged batches, padded strides,
+the same operands, bit for bit.  Covers every kernel shape (2 to 65 result
+registers per lane, 0 to 4 shared stages), positions 0 and n - 1, w = 0,
+ragged batches, padded strides,
 garbage above n, rejections, and launch times independent of the positions."""
 import time
 
@@ -37,12 +37,17 @@ def _positions(seed: int, n: int, w: int, count: int) -> np.ndarray:
 
 
 @pytest.mark.parametrize("n,w,count", [
-    (17669, 75, 37),      # HQC-128 shape, D in registers (35 words per lane)
-    (35851, 114, 9),      # staged kernel, no shared stage
-    (57637, 131, 5),      # staged kernel, two shared stages
+    (17669, 75, 37),      # HQC-128 shape: 18 result registers per lane, no shared stage
+    (35851, 114, 9),      # 36 result registers, six register stages
+    (57637, 131, 5),      # 57 result registers, two shared stages
     (65536, 16, 3),       # four shared stages, largest n
-    (8673, 40, 33),       # 17 words per lane
-    (4577, 20, 65),       # 9 words per lane
+    (60000, 50, 3),       # 65 result registers, three shared stages
+    (40973, 137, 5),      # 46 result registers, two shared stages (BIKE-5 size)
+    (24659, 103, 9),      # 26 result registers (BIKE-3 size)
+    (12323, 71, 17),      # 13 result registers (BIKE-1 size)
+    (8673, 40, 33),       # 9 result registers
+    (4577, 20, 65),       # 5 result registers
+    (2017, 9, 5), (2016, 8, 5),   # the two sides of the smallest shape's limit
     (100, 7, 3), (33, 5, 2), (32, 3, 2), (31, 4, 2), (1, 1, 2),
 ])
 def test_matches_oracle_and_dense_path(n, w, count):

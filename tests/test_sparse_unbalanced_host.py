@@ -1,10 +1,11 @@
 """Host-side checks of the sparse and unbalanced products (no GPU).
 
 * The shape the library picks for the constant-time sparse kernel, for
-  every n it accepts: the warp's cyclic window holds every word a position
-  can read, the shared-memory shifts are the in-place-safe ones (>= 256
-  words), the stages cover all bits of the word offset, and the shared
-  memory fits a CTA.
+  every n it accepts: the result registers hold every result word and the
+  funnel's neighbour, the register window holds every word a register
+  offset can reach, the shared-memory shifts are the in-place-safe ones
+  (>= 256 words), the stages cover all bits of the word offset, and the
+  shared memory fits a CTA.
 * The two identities the kernels are built on, checked with the oracle on
   small random cases: rot(a, p) is the n-bit window at bit n - p of
   a + X^n a; and a b = sum_i (a_i b) X^(i m) for a's m-bit chunks a_i."""
@@ -27,15 +28,17 @@ def test_sparse_shape_for_every_n():
         s = gf2x.sparse_info(n)
         N, qmax = (n + 31) // 32, n >> 5
         T = qmax.bit_length()
-        C = s["words_per_lane"]
-        assert s["shared_stages"] + s["register_stages"] == T, n
-        assert C % 2 == 1, n                           # lane-strided shared accesses avoid bank conflicts
-        if s["shared_stages"] == 0:
-            assert 32 * C >= N + qmax + 1, n           # every read index i + q <= N + n/32 stays in the window
+        C, R, pre = s["words_per_lane"], s["result_words_per_lane"], s["shared_stages"]
+        QH = C - R - 1
+        assert 32 * R >= N + 1, n                      # result words and the funnel's neighbour word
+        assert QH >= 0 and s["register_stages"] == QH.bit_length(), n
+        assert s["lane_stages"] == 5, n
+        if pre == 0:
+            assert (qmax >> 5) <= QH, n                # every whole-register offset stays in the window
         else:
-            assert s["doubled_in_registers"] == 0, n
-            assert (1 << s["register_stages"]) >= 256, n     # in-place shared shifts read 256 words ahead
-            assert 32 * C >= N + (1 << s["register_stages"]), n
+            assert (1 << (T - pre)) == 32 * (QH + 1), n   # the shared stages leave offsets < 32 (QH + 1)
+            assert (1 << (T - pre)) >= 256, n          # in-place shared shifts read 256 words ahead
+        assert pre + s["register_stages"] + 5 >= T, n  # the stages cover every bit of the word offset
         assert s["smem_bytes"] <= 227 * 1024, n
     for bad in (0, 65537, 1 << 20):
         with pytest.raises(gf2x.Gf2xError):
