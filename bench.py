@@ -592,22 +592,24 @@ def run_c3(device):
     log = autotune.packaged_log()
 
     def time_mixed(plans):
-        """One graph-replayed persistent launch over the device items: as
+        """One graph-replayed launch over the device items: persistent as
         interleaved (static stride), largest first (static stride), largest
-        first with CTAs taking items from a counter (dynamic)."""
+        first with CTAs taking items from a counter (dynamic); and one CTA
+        per item, largest first."""
         ctx = Context(device, plan_db=None)
         for n, sp in plans.items():
             ctx.set_plan(int(n), sp)
         ctx.prepare(sorted(int(n) for n in weights))
         stream = torch.cuda.Stream()
         res = []
-        for its, dyn in ((items, False), (items_lf, False), (items_lf, True)):
+        for its, pers, dyn in ((items, True, False), (items_lf, True, False), (items_lf, True, True),
+                               (items_lf, False, False)):
             with torch.cuda.stream(stream):
-                ctx.mul_batched_device(its, len(sizes), persistent=True, dynamic=dyn)
+                ctx.mul_batched_device(its, len(sizes), persistent=pers, dynamic=dyn)
             torch.cuda.synchronize()
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream):
-                ctx.mul_batched_device(its, len(sizes), persistent=True, dynamic=dyn)
+                ctx.mul_batched_device(its, len(sizes), persistent=pers, dynamic=dyn)
             res.append(_time_calls(g.replay, 10, 3))
         ctx.sync_status()
         ctx.close()
@@ -628,7 +630,7 @@ def run_c3(device):
             timed.append((min(t), origin, plans, t))
     best_log = min((x for x in timed if x[1] == "log"), key=lambda x: x[0])
     best_model = min((x for x in timed if x[1] == "model"), key=lambda x: x[0])
-    _, _, plans, (ms, ms_lf, ms_dyn) = min(timed, key=lambda x: x[0])
+    _, _, plans, (ms, ms_lf, ms_dyn, ms_cta) = min(timed, key=lambda x: x[0])
     model_regret = best_model[0] / best_log[0] - 1.0
     best = (ms, plans, min(ms_lf, ms_dyn))
     ms, plans, ms_lf = best
@@ -668,42 +670,52 @@ def run_c3(device):
     ms_grouped = _time_calls(grouped, 10, 3)
     ctx2.close()
     # ONE graph launch: the per-size tuned kernels (split plans included) on
-    # forked streams, so that the sizes overlap on the GPU; one context per
-    # size keeps the split scratch of each on its own stream
-    sizes_n = [int(n) for n in weights]
-    ctxs = {n: Context(device, batch_hint=2048) for n in sizes_n}
-    branch = {n: torch.cuda.Stream() for n in sizes_n}
-    root = torch.cuda.Stream()
-    for n in sizes_n:                         # warm-up on the streams the graph will use
-        with torch.cuda.stream(branch[n]):
-            ctxs[n].mul_strided(reqs.a[n], reqs.b[n], n, True, out=outs[n], persistent=True)
-    torch.cuda.synchronize()
-    g2 = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g2, stream=root):
-        fork = torch.cuda.Event()
-        fork.record(root)
-        for n in sizes_n:
-            branch[n].wait_event(fork)
+    # forked streams, largest n first, so that the sizes overlap on the GPU;
+    # one context per size keeps the split scratch of each on its own
+    # stream.  One CTA per product lets the block scheduler interleave the
+    # three kernels' CTAs; persistent grids each fill the GPU, so the later
+    # kernels mostly run in the first one's tail.
+    sizes_n = sorted((int(n) for n in weights), reverse=True)
+
+    def forked_graph(persistent):
+        ctxs = {n: Context(device, batch_hint=2048) for n in sizes_n}
+        branch = {n: torch.cuda.Stream() for n in sizes_n}
+        root = torch.cuda.Stream()
+        for n in sizes_n:                         # warm-up on the streams the graph will use
             with torch.cuda.stream(branch[n]):
-                ctxs[n].mul_strided(reqs.a[n], reqs.b[n], n, True, out=outs[n], persistent=True)
-        for n in sizes_n:
-            root.wait_stream(branch[n])
-    for o in outs.values():
-        o.zero_()
-    ms_graph = _time_calls(g2.replay, 10, 3)
-    ok_graph = True
-    for r in range(0, len(sizes), 149):
-        n, i = int(sizes[r]), int(reqs.index[r])
-        ok_graph &= bool(np.array_equal(_host(outs[n][i]), oracle.mulmod(_host(reqs.a[n][i]), _host(reqs.b[n][i]), n)))
-    for c in ctxs.values():
-        c.close()
+                ctxs[n].mul_strided(reqs.a[n], reqs.b[n], n, True, out=outs[n], persistent=persistent)
+        torch.cuda.synchronize()
+        g2 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g2, stream=root):
+            fork = torch.cuda.Event()
+            fork.record(root)
+            for n in sizes_n:
+                branch[n].wait_event(fork)
+                with torch.cuda.stream(branch[n]):
+                    ctxs[n].mul_strided(reqs.a[n], reqs.b[n], n, True, out=outs[n], persistent=persistent)
+            for n in sizes_n:
+                root.wait_stream(branch[n])
+        for o in outs.values():
+            o.zero_()
+        ms_g = min(_time_calls(g2.replay, 10, 3) for _ in range(2))
+        ok_g = True
+        for r in range(0, len(sizes), 149):
+            n, i = int(sizes[r]), int(reqs.index[r])
+            ok_g &= bool(np.array_equal(_host(outs[n][i]), oracle.mulmod(_host(reqs.a[n][i]), _host(reqs.b[n][i]), n)))
+        for c in ctxs.values():
+            c.close()
+        return ms_g, ok_g
+    ms_graph_p, ok_graph_p = forked_graph(True)
+    ms_graph, ok_graph = forked_graph(False)
     total = len(sizes)
     return {"workload": wk.name, "products": total, "plans": {str(k): v for k, v in plans.items()},
             "one_launch_graph_mults_per_s": total / (ms * 1e-3),
             "one_launch_graph_largest_first_mults_per_s": total / (ms_lf * 1e-3),
+            "one_launch_graph_one_cta_per_item_mults_per_s": total / (ms_cta * 1e-3),
             "one_launch_schedule": "largest first, items from a counter" if dyn_best else "largest first, static stride",
             "plan_sets_timed": [{"origin": o, "plans": {str(k): v for k, v in p.items()},
-                                 "interleaved_ms": t[0], "largest_first_ms": t[1], "largest_first_dynamic_ms": t[2]}
+                                 "interleaved_ms": t[0], "largest_first_ms": t[1], "largest_first_dynamic_ms": t[2],
+                                 "one_cta_per_item_ms": t[3]}
                                 for _, o, p, t in timed],
             "model_proposed_best_mults_per_s": total / (best_model[0] * 1e-3),
             "log_best_mults_per_s": total / (best_log[0] * 1e-3),
@@ -711,8 +723,10 @@ def run_c3(device):
             "plain_mults_per_s": total / (ms_plain * 1e-3),
             "per_size_launches_mults_per_s": total / (ms_grouped * 1e-3),
             "one_graph_concurrent_per_size_kernels_mults_per_s": total / (ms_graph * 1e-3),
+            "one_graph_form": "forked streams, largest n first, one CTA per product",
+            "one_graph_persistent_kernels_mults_per_s": total / (ms_graph_p * 1e-3),
             "graph_plans": {str(n): ctx_plan_text(n, 2048) for n in sizes_n},
-            "sample_checked_against_oracle": ok and ok_graph}
+            "sample_checked_against_oracle": ok and ok_graph and ok_graph_p}
 
 
 def run_c4(device):
