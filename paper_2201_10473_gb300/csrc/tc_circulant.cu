@@ -31,9 +31,10 @@
 //                     accumulator buffers, so a unit's parities are read
 //                     while the next unit accumulates; the parities go out
 //                     in position-index (q) order;
-//  tc_assemble_kernel q order -> bit order: r_j[p] = parity[j][q(p)], a
-//                     funnel-shift gather of each bit column and a warp
-//                     butterfly transpose per 32 output words.
+//  tc_assemble_kernel q order -> bit order: r_j[p] = parity[j][q(p)], the
+//                     row staged in shared memory, a funnel-shift gather of
+//                     each bit column and a warp butterfly transpose per 32
+//                     output words.
 // Constant time: every loop bound, address and branch depends on n, count
 // and thread indices only; operand bits flow through data paths.
 // Every wait on a barrier is bounded (globaltimer); on a timeout the CTA
@@ -421,61 +422,77 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const TcGemmArgs
 
 // r_j in bit order from the parities in q order: for output words w0 .. w0+31
 // and bit e, q(32 w + e) = (Q_e - w) mod n with Q_e = (n - 1 - e) inv32 mod n,
-// a run of 32 q's read backwards; lane e gathers it (funnel shift, or bit by
-// bit where it wraps past q = 0), the warp transposes by ballots.
+// a run of 32 q's read backwards from start = (Q_e - w0 - 31) mod n; lane e
+// gathers it with one funnel shift, the warp transposes it.  One CTA per
+// product at a time: the product's parity row is first copied to shared
+// memory (coalesced), followed by its first bits again from bit n on, so
+// that no run wraps past q = n - 1.  Warp k takes the 32-word blocks k, k + 8,
+// ..., so a lane's run start moves down by 256 from one block to the next
+// (start computed once per thread, no division per block).
 __global__ void __launch_bounds__(256) tc_assemble_kernel(const uint32_t *__restrict__ qbits, uint32_t qwords,
                                                           uint32_t n, uint32_t inv32, uint32_t count,
                                                           uint64_t *__restrict__ out, size_t stride_out)
 {
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t L32 = (n + 31) / 32, blocks = (L32 + 31) / 32;
-    const uint32_t Qe = (uint32_t)(((uint64_t)(n - 1u - (lane % n)) % n * inv32) % n);
-    // warps walk the 32-word blocks of one product after the other (j advances
-    // when blk wraps): no 64-bit division per task
-    const uint32_t wstep = gridDim.x * (blockDim.x / 32);
-    uint32_t wid = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    uint32_t j = wid / blocks, blk = wid - j * blocks;
-    const uint32_t jstep = wstep / blocks, bstep = wstep - jstep * blocks;
-    for (; j < count; j += jstep, blk += bstep) {
-        if (blk >= blocks) {
-            blk -= blocks;
-            ++j;
-            if (j >= count)
-                break;
-        }
-        const uint32_t w0 = blk * 32u;
+    extern __shared__ uint32_t srow[];   // (n >> 5) + 2 words
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t L32 = (n + 31) / 32, blocks = (L32 + 31) / 32, W32 = 2u * ((n + 63u) / 64u);
+    const uint32_t nw = n >> 5, sft = n & 31u;   // n is odd: sft > 0
+    // n <= 65535 and inv32 < n: the products stay below 2^32
+    const uint32_t Qe = ((n - 1u - (lane % n)) * inv32) % n;
+    const uint32_t start0 = (Qe + 32u * n - 32u * warp - 31u) % n;   // first block of this warp (32 warp < n)
+    const uint32_t step = (32u * nwarps) % n;
+    // per transpose stage s (16, 8, 4, 2, 1): a lane with bit s set takes the
+    // partner's word shifted right by s into its low s-blocks, the others
+    // its word shifted left into their high s-blocks; a rotation by the
+    // lane's amount puts the wanted bits in place (the wrapped bits fall
+    // under the mask), and `keep` selects the lane's own bits
+    uint32_t keep[5], rot[5];
+#pragma unroll
+    for (uint32_t t = 0, sh = 16, m = 0x0000ffffu; t < 5; ++t, sh >>= 1, m ^= m << sh) {
+        keep[t] = (lane & sh) ? ~m : m;
+        rot[t] = (lane & sh) ? 32u - sh : sh;
+    }
+    for (uint32_t j = blockIdx.x; j < count; j += gridDim.x) {
+        // the row's words below nw, then the two words from bit 32 nw on,
+        // where bits n .. n + 62 repeat the row's bits 0 .. 62 (the row is
+        // periodic in q with period n), so that no run wraps past q = n - 1
         const uint32_t *row = qbits + (size_t)j * qwords;
-        // q run: start = (Q_e - w0 - 31) mod n, 32 bits (n <= 65535: 32-bit arithmetic)
-        const uint32_t start = (Qe + 32u * n - (w0 % n) - 31u) % n;
-        uint32_t x;
-        if (start + 31u < n) {
-            const uint32_t lo = row[start >> 5], hi = row[(start >> 5) + 1u];
-            x = __funnelshift_r(lo, hi, start & 31u);
-        } else {   // the run wraps past q = n - 1 (sizes only decide this)
-            x = 0;
-            uint32_t q = start;
-            for (uint32_t i = 0; i < 32u; ++i) {
-                x |= ((row[q >> 5] >> (q & 31u)) & 1u) << i;
-                q = q + 1u == n ? 0u : q + 1u;
+        for (uint32_t i = threadIdx.x; i < nw + 2u; i += blockDim.x) {
+            uint32_t v;
+            if (i < nw)
+                v = row[i];
+            else if (i == nw)   // bits below n, then the row's bits 0 .. 31 - sft
+                v = (row[nw] & ((1u << sft) - 1u)) | (row[0] << sft);
+            else
+                v = (row[0] >> (32u - sft)) | (row[1] << sft);
+            srow[i] = v;
+        }
+        __syncthreads();
+        uint32_t *o = reinterpret_cast<uint32_t *>(out + (size_t)j * stride_out);
+        uint32_t st = start0;
+        for (uint32_t blk = warp; blk < blocks; blk += nwarps) {
+            const uint32_t x = __funnelshift_r(srow[st >> 5], srow[(st >> 5) + 1u], st & 31u);
+            st = st >= step ? st - step : st + n - step;
+            // lane e holds bit e of words w0 .. w0+31 (bit i <-> word w0 + i);
+            // a 32 x 32 bit transpose across the warp (swap the off-diagonal
+            // s x s blocks for s = 16, 8, 4, 2, 1) leaves word w0 + lane in lane
+            uint32_t mine = __brev(x);
+#pragma unroll
+            for (uint32_t t = 0, sh = 16; t < 5; ++t, sh >>= 1) {
+                const uint32_t y = __shfl_xor_sync(0xffffffffu, mine, sh);
+                const uint32_t r = __funnelshift_l(y, y, rot[t]);
+                mine = (mine & keep[t]) | (r & ~keep[t]);
+            }
+            const uint32_t w = 32u * blk + lane;
+            if (w < L32) {
+                if (w == L32 - 1u)
+                    mine &= (1u << sft) - 1u;
+                o[w] = mine;
+            } else if (w < W32) {
+                o[w] = 0u;   // the top limb's upper half
             }
         }
-        // lane e holds bit e of words w0 .. w0+31 (bit i <-> word w0 + i);
-        // a 32 x 32 bit transpose across the warp (swap the off-diagonal
-        // s x s blocks for s = 16, 8, 4, 2, 1) leaves word w0 + lane in lane
-        uint32_t mine = __brev(x);
-#pragma unroll
-        for (uint32_t sh = 16, m = 0x0000ffffu; sh > 0; sh >>= 1, m ^= m << sh) {
-            const uint32_t y = __shfl_xor_sync(0xffffffffu, mine, sh);
-            mine = (lane & sh) ? ((mine & ~m) | ((y >> sh) & m)) : ((mine & m) | ((y << sh) & ~m));
-        }
-        const uint32_t w = w0 + lane;
-        if (w < L32) {
-            if (w == L32 - 1u && (n & 31u))
-                mine &= (1u << (n & 31u)) - 1u;
-            reinterpret_cast<uint32_t *>(out + (size_t)j * stride_out)[w] = mine;
-        } else if (w < 2u * ((n + 63u) / 64u)) {
-            reinterpret_cast<uint32_t *>(out + (size_t)j * stride_out)[w] = 0u;   // the top limb's upper half
-        }
+        __syncthreads();   // srow is rewritten for the next product
     }
 }
 
@@ -551,8 +568,7 @@ cudaError_t launch_tc_group(const uint64_t *b, size_t stride_b, uint64_t *out, s
     e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    const uint64_t tasks = (uint64_t)count * (((n + 31) / 32 + 31) / 32);
-    tc_assemble_kernel<<<(unsigned)std::min<uint64_t>(16ull * sm_count, (tasks + 7) / 8), 256, 0, st>>>(
+    tc_assemble_kernel<<<(unsigned)std::min<uint64_t>(8ull * sm_count, count), 256, 4u * (n / 32u + 2u), st>>>(
         qbits, sh.qwords, n, sh.inv32, count, out, stride_out);
     return cudaGetLastError();
 }
