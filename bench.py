@@ -2,8 +2,11 @@
 
 Default workload: 4096 products of dense Bernoulli(0.5) polynomials with
 n = 17669 coefficients (HQC-128 size), reduced mod X^n - 1, in ONE batched
-persistent launch per step (the batched form); the plain form (one launch
-per product) is measured beside it.  One JSON line on stdout (rank 0).
+launch per step (one CTA per product: the block scheduler spreads the
+products of a partial last round over the SMs); the persistent form of the
+same launch (a grid of resident CTAs taking products from a counter) and
+the plain form (one launch per product) are measured beside it.  One JSON
+line on stdout (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload hqc128|hqc192|hqc256|c1] [--no-plain]
@@ -214,7 +217,7 @@ def config_of(w, spec, shape):
     if spec:
         c["plan"] = spec
     if shape:
-        c["launch"] = dict(shape, persistent=True)
+        c["launch"] = dict(shape, form="one batched launch, one CTA per product")
     return c
 
 
@@ -309,9 +312,9 @@ def run_ours(args, w):
     out = torch.empty((batch, ol), dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(i):
+    def step(i, persistent=False):
         a, b = sets[i % R]
-        ctx.mul_strided(a, b, n, reduce, out=out, persistent=True, stream=stream)
+        ctx.mul_strided(a, b, n, reduce, out=out, persistent=persistent, stream=stream)
 
     # parity spot check of this run's launch configuration before timing
     import_oracle_ok = True
@@ -400,6 +403,30 @@ def run_ours(args, w):
         if not e2e_ok:
             raise SystemExit("bench: host-buffer (e2e) results differ from the oracle")
 
+    # ---- the persistent form of the batched launch (a grid of resident CTAs
+    # taking the products in order from a counter), same inputs and plan
+    Kp = max(3, min(K, 400))
+    for i in range(3):
+        step(i, persistent=True)
+    torch.cuda.synchronize()
+    q0 = torch.cuda.Event(enable_timing=True)
+    q1 = torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for i in range(Kp):
+        step(i, persistent=True)
+    q1.record(stream)
+    torch.cuda.synchronize()
+    pers_ms = shard.max_over_ranks(q0.elapsed_time(q1), device="cuda")
+    persistent_form = {"mults_per_s": shard.whole_job_rate(batch * Kp, world, pers_ms * 1e-3), "steps": Kp,
+                       "grid": int(shape["blocks_per_sm"]) * int(shape["sm_count"]),
+                       "order": "CTAs take the products in order from a counter"}
+    if rank == 0 and import_oracle_ok:
+        import oracle
+        sample = np.arange(0, batch, max(1, batch // 16))
+        if not np.array_equal(out.cpu().numpy().view(np.uint64)[sample],
+                              oracle.mul_batch(host_a[sample], host_b[sample], n, reduce=reduce)):
+            raise SystemExit("bench: persistent-launch results differ from the oracle")
+
     # ---- plain form: one launch of one CTA per product, with the plan tuned
     # for a single product per launch
     plain = None
@@ -486,6 +513,7 @@ def run_ours(args, w):
         "gpu_launches": K * launches_per_step(info, batch),
         "roofline": roof,
         "cpu_baseline": cpu,
+        "persistent_launch": persistent_form,
         "plain": plain,
         "batched_over_plain": (value / world / plain["value"]) if plain else None,
         "clocks": clk,
