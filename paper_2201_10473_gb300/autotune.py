@@ -4,7 +4,8 @@ The autotuner enumerates recursion plans for a size n (optional Toom-3 top
 level with several word shifts, non-increasing Karatsuba split sequences,
 every compiled leaf size, fused or shared-memory last level, breadth-first or
 sequential top, several CTA sizes), measures each on the GPU with CUDA events
-in the launch form it will be used in (one persistent batched launch), and
+in the launch form it will be used in (one batched launch: a persistent grid,
+or one CTA per product with --launch cta), and
 keeps the fastest.  Every measurement is appended to a JSONL timing log,
 which also trains the learned cost model (costmodel.py).
 
@@ -97,11 +98,13 @@ class Measurement:
 class Autotuner:
     """Times plan specs for one context; appends every timing to `log_path`."""
 
-    def __init__(self, ctx: gf2x.Context, log_path: str | None = None, reps: int = 5, warmup: int = 2):
+    def __init__(self, ctx: gf2x.Context, log_path: str | None = None, reps: int = 5, warmup: int = 2,
+                 persistent: bool = True):
         import torch
         self.torch = torch
         self.ctx = ctx
         self.log_path = log_path
+        self.persistent = persistent   # the launch form timed (False: one CTA per product)
         self.reps = reps
         self.warmup = warmup
         self._inputs = {}
@@ -128,8 +131,9 @@ class Autotuner:
             self._inputs[key] = (a, b, out, ref, chk)
         return self._inputs[key]
 
-    def measure(self, n: int, spec: str, batch: int, persistent: bool = True, verify: bool = True) -> Measurement:
+    def measure(self, n: int, spec: str, batch: int, persistent: bool | None = None, verify: bool = True) -> Measurement:
         torch = self.torch
+        persistent = self.persistent if persistent is None else persistent
         a, b, out, ref, chk = self._operands(n, batch)
         m = ref.shape[0]
         prev = self.ctx.get_plan(n)
@@ -165,7 +169,7 @@ class Autotuner:
         info = gf2x.plan_info(m.n, m.spec)
         rec = dict(m.__dict__)
         rec.update(ts=time.time(), ops_full=info["ops_full"], top_words=info["top_words"],
-                   nleaves=info["nleaves"])
+                   nleaves=info["nleaves"], launch="persistent" if self.persistent else "cta")
         os.makedirs(os.path.dirname(os.path.abspath(self.log_path)), exist_ok=True)
         with open(self.log_path, "a") as f:
             f.write(json.dumps(rec) + "\n")
@@ -280,6 +284,17 @@ PACKAGED_SINGLE_LOG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "
                                    "gb300_timing_log_batch1.jsonl.gz")
 
 
+# top plans of the exhaustive log re-measured in the one-CTA-per-product
+# launch form (--launch cta), batches 2048 and 4096 of the six serving sizes
+PACKAGED_CTA_LOG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans", "gb300_timing_log_cta.jsonl.gz")
+
+
+def packaged_cta_log() -> list:
+    import gzip
+    with gzip.open(PACKAGED_CTA_LOG, "rt") as f:
+        return [json.loads(line) for line in f if line.strip()]
+
+
 def single_product_plans(sizes, one_launch: bool = True) -> dict:
     """Fastest plan for one product per launch of every size, from the batch-1
     timing log; one_launch excludes split plans (three launches)."""
@@ -369,6 +384,8 @@ def main(argv=None):
                                                      "('packaged' = the shipped GB300 log)")
     p.add_argument("--top", type=int, default=60)
     p.add_argument("--split-from", type=int, default=24000, help="also try split-top plans from this size on")
+    p.add_argument("--launch", choices=["persistent", "cta"], default="persistent",
+                   help="launch form timed: a persistent grid (products from a counter) or one CTA per product")
     p.add_argument("--guided", type=int, default=0,
                    help="measure only the K candidates a cost model (trained on the packaged log) ranks first")
     a = p.parse_args(argv)
@@ -386,7 +403,7 @@ def main(argv=None):
     batches = [int(x) for x in a.batches.split(",") if x]
     for n in sizes:
         ctx = gf2x.Context()          # a fresh plan table per size
-        tuner = Autotuner(ctx, a.log)
+        tuner = Autotuner(ctx, a.log, persistent=a.launch == "persistent")
         cands = candidate_specs(n, limit=a.limit, split_from=a.split_from)
         if prior is not None:
             ranked = sorted((r for r in prior if r["n"] == n and r["batch"] == batches[0]), key=lambda r: r["ms"])

@@ -198,8 +198,10 @@ def test_split_plan_facts():
 
 def test_packaged_plan_database_and_logs_are_consistent():
     """Every database entry is a valid plan for its size and is the fastest
-    record of its (size, bucket) in the shipped timing logs; the single-
-    product plans chosen for the plain baselines are one-launch plans."""
+    record of its (size, bucket) in the shipped timing logs -- of the
+    one-CTA-per-product log where that log covers the bucket, else of the
+    persistent-launch logs; the single-product plans chosen for the plain
+    baselines are one-launch plans."""
     import gzip
     import json
 
@@ -208,11 +210,15 @@ def test_packaged_plan_database_and_logs_are_consistent():
     recs = autotune.packaged_log()
     with gzip.open(autotune.PACKAGED_SINGLE_LOG, "rt") as f:
         recs += [json.loads(line) for line in f if line.strip()]
+    cta = autotune.packaged_cta_log()
+    assert cta and all(r["launch"] == "cta" for r in cta)
     assert len(db) >= 24
     for (n, bucket), e in db.items():
         info = gf2x.plan_info(n, e["spec"])
         assert 32 * info["top_words"] >= n
-        same = [r for r in recs if r["n"] == n and autotune.batch_bucket(r["batch"]) == bucket]
+        same = [r for r in cta if r["n"] == n and autotune.batch_bucket(r["batch"]) == bucket]
+        if not same:
+            same = [r for r in recs if r["n"] == n and autotune.batch_bucket(r["batch"]) == bucket]
         assert same, (n, bucket)
         assert min(same, key=lambda r: r["ms"])["spec"] == e["spec"], (n, bucket)
     single = autotune.single_product_plans([12323, 17669, 24659, 35851, 40973, 57637])
