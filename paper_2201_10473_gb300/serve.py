@@ -342,9 +342,10 @@ class SizeAwareServer:
     Admission, slots and retirement as in Server."""
 
     def __init__(self, plans: dict, budget_bytes: int, max_batch: int = 2048, streams_per_size: int = 2,
-                 min_bucket: int = 32, device: int = 0):
+                 min_bucket: int = 32, device: int = 0, persistent: bool = True):
         import torch
         self.torch = torch
+        self.persistent = persistent   # False: one CTA per item slot (empty slots exit at once)
         self.sizes = sorted(plans)
         self.max_batch = max_batch
         fixed = len(self.sizes) * streams_per_size * max_batch * (4 + 6) * 8   # item and copy lists
@@ -397,7 +398,7 @@ class SizeAwareServer:
         self.rows_dev[(n, s)][:2 * count].copy_(self.rows_host[(n, s)][:2 * count], non_blocking=True)
         self.items_dev[(n, s)][:count].copy_(self.items_host[(n, s)][:count], non_blocking=True)
         self.ctx[n].copy_rows(self.rows_dev[(n, s)], 2 * count, stream=st)     # operands into their slots
-        self.ctx[n].mul_batched_device(self.items_dev[(n, s)], count, persistent=True, stream=st)
+        self.ctx[n].mul_batched_device(self.items_dev[(n, s)], count, persistent=self.persistent, stream=st)
 
     def _bucket(self, k: int) -> int:
         for b in self.buckets:
