@@ -109,7 +109,7 @@ typedef struct {
     uint32_t level_words[GF2X_MAX_LEVELS + 1]; /* operand size at each depth (top first, leaf last) */
     uint64_t ops_full;           /* modelled 32-bit integer operations per full product */
     uint64_t ops_leaf;           /* of which in the leaf schoolbook */
-    uint64_t clmul64;            /* 64x64-bit word products (Table tab:compKarat); leaf_words even */
+    uint64_t clmul64;            /* 64x64-bit word products (the Karatsuba-variants complexity table of Sec. 2.1); leaf_words even */
     uint64_t bytes_in;           /* HBM bytes read per product */
     uint64_t bytes_out_full;     /* HBM bytes written, full product */
     uint64_t bytes_out_reduced;  /* HBM bytes written, reduced product */
@@ -264,9 +264,14 @@ gf2x_status gf2x_mul_strided(gf2x_ctx *ctx, uint64_t *out, const uint64_t *a, co
  *    next item from a device counter of the context (zeroed by a memset on
  *    `stream` before the launch, which a CUDA graph captures as well), so
  *    items are started in array order as CTAs free up -- with items sorted
- *    largest first this is longest-processing-time-first scheduling.  The
- *    context has 256 counters used round robin: more than 256 dynamic
- *    launches in flight at once on different streams would share one. */
+ *    largest first this is longest-processing-time-first scheduling.
+ *    Outside a stream capture the context's 256 counters are used round
+ *    robin, and a counter's next launch first waits (on its stream) for the
+ *    event recorded behind its previous launch, whatever stream that was
+ *    on.  A captured launch keeps a counter of its own for the graph's
+ *    lifetime (1024 per context; beyond that, captured launches take items
+ *    in the static order i, i + grid, ...).  Replays of one graph must not
+ *    overlap each other. */
 gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, size_t count,
                              uint32_t batch_flags, gf2x_stream stream);
 
@@ -501,7 +506,7 @@ gf2x_status gf2x_mul_strided_static(uint64_t *out, const uint64_t *a, const uint
  * A two-layer perceptron y = w2 . relu(W1 x + b1) + b2 in fp32 that predicts
  * the log time of a recursion plan from its descriptor.  The paper has no
  * counterpart: it chooses constructions per degree by measurement (Sec. 3,
- * Tables tab:perfToom3KR, tab:perfCompToom3K3); the network only orders the
+ * the Toom-3 timing tables of Sec. 3.2 and 3.3); the network only orders the
  * candidates the autotuner measures.  All pointers are device pointers; the
  * parameter vector is W1 [hidden x in_dim] row-major, b1 [hidden],
  * w2 [hidden], b2 [1] (gf2x_mlp_param_count floats).  1 <= in_dim <= 64,

@@ -35,7 +35,13 @@ struct PlanEntry {
 
 constexpr uint64_t kWorkspaceCap = 256ull << 20;  // split plans run in chunks of at most this much scratch
 constexpr size_t kFixedStagingItems = 16384;      // item staging per ring buffer in a fixed-workspace context
-constexpr uint32_t kCounters = 256;               // work counters of dynamic launches (reused round robin)
+// Work counters of dynamic launches: a ring for launches made outside a
+// stream capture (a slot is reused only after the event recorded behind its
+// last launch), and slots that a captured launch keeps for the graph's
+// lifetime (never reused; when they run out, a captured persistent launch
+// uses the static order instead).
+constexpr uint32_t kCounters = 256;
+constexpr uint32_t kGraphCounters = 1024;
 
 // Allocation failures injected on the host (tests of the GF2X_ENOMEM paths):
 // the next g_fail_allocs allocations of any context fail without a CUDA call.
@@ -99,6 +105,9 @@ struct gf2x_ctx {
     bool ub_used = false;
     uint32_t *counters = nullptr;                       // work counters of dynamic launches (a ring)
     uint32_t counter_next = 0;
+    cudaEvent_t counter_ev[kCounters] = {};               // recorded behind the last launch on each ring slot
+    bool counter_used[kCounters] = {};
+    uint32_t graph_counter_next = 0;                      // next never-reused slot for captured launches
     bool fixed = false;                                 // workspace fixed at creation: compute calls allocate nothing
     void *arena = nullptr;                              // the fixed workspace (split | unbalanced/Toom | host pipeline)
     uint64_t allocs = 0;                                // device and pinned allocations made by the context
@@ -223,7 +232,10 @@ extern "C" gf2x_status gf2x_ctx_create(gf2x_ctx **out, int device, size_t worksp
         e = cudaMemset(ctx->err_dev, 0, sizeof(uint32_t));
     alloc((void **)&ctx->plan_of_n_host, sizeof(uint32_t) * (GF2X_MAX_N + 1), true);
     alloc((void **)&ctx->plan_of_n_dev, sizeof(uint32_t) * (GF2X_MAX_N + 1), false);
-    alloc((void **)&ctx->counters, sizeof(uint32_t) * kCounters, false);
+    alloc((void **)&ctx->counters, sizeof(uint32_t) * (kCounters + kGraphCounters), false);
+    for (auto &ev : ctx->counter_ev)
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) {
         memset(ctx->plan_of_n_host, 0xff, sizeof(uint32_t) * (GF2X_MAX_N + 1));
         e = cudaMemset(ctx->plan_of_n_dev, 0xff, sizeof(uint32_t) * (GF2X_MAX_N + 1));
@@ -338,6 +350,9 @@ extern "C" void gf2x_ctx_destroy(gf2x_ctx *ctx)
         cudaFree(ctx->plan_of_n_dev);
     if (ctx->counters)
         cudaFree(ctx->counters);
+    for (cudaEvent_t ev : ctx->counter_ev)
+        if (ev)
+            cudaEventDestroy(ev);
     if (ctx->arena) {   // ws, ub and hp.buf live in it
         cudaFree(ctx->arena);
     } else {
@@ -556,6 +571,7 @@ static gf2x_status launch(gf2x_ctx *ctx, const LaunchArgs &args, uint32_t S, uns
         return fail(ctx, GF2X_EUNSUPPORTED, "leaf size not compiled");
     unsigned grid;
     LaunchArgs a = args;
+    int ring_slot = -1;   // counter ring slot of an uncaptured dynamic launch
     if (persistent) {
         // cached so that launches inside a CUDA graph capture make no occupancy query
         const uint64_t okey = ((uint64_t)S << 48) | ((uint64_t)threads << 32) | (uint64_t)smem;
@@ -574,11 +590,28 @@ static gf2x_status launch(gf2x_ctx *ctx, const LaunchArgs &args, uint32_t S, uns
         grid = (unsigned)std::min<size_t>(count, (size_t)per_sm * ctx->sm_count);
         a.persistent = 1;
         if (dynamic && grid > 0) {   // items in order from a counter zeroed on the stream (a graph node too)
-            uint32_t *c = ctx->counters + (ctx->counter_next++ % kCounters);
-            cudaError_t e = cudaMemsetAsync(c, 0, sizeof(uint32_t), stream);
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            cudaError_t e = cudaStreamIsCapturing(stream, &cs);
             if (e != cudaSuccess)
-                return cuda_fail(ctx, e, "work counter reset");
-            a.work_counter = c;
+                return cuda_fail(ctx, e, "capture status");
+            uint32_t *c = nullptr;
+            if (cs != cudaStreamCaptureStatusNone) {
+                if (ctx->graph_counter_next < kGraphCounters)
+                    c = ctx->counters + kCounters + ctx->graph_counter_next++;
+            } else {
+                ring_slot = (int)(ctx->counter_next++ % kCounters);
+                if (ctx->counter_used[ring_slot])   // its previous launch (any stream) has finished with it
+                    e = cudaStreamWaitEvent(stream, ctx->counter_ev[ring_slot], 0);
+                if (e != cudaSuccess)
+                    return cuda_fail(ctx, e, "work counter wait");
+                c = ctx->counters + ring_slot;
+            }
+            if (c) {
+                e = cudaMemsetAsync(c, 0, sizeof(uint32_t), stream);
+                if (e != cudaSuccess)
+                    return cuda_fail(ctx, e, "work counter reset");
+                a.work_counter = c;
+            }
         }
     } else {
         if (count > 0x7fffffffu)
@@ -591,6 +624,12 @@ static gf2x_status launch(gf2x_ctx *ctx, const LaunchArgs &args, uint32_t S, uns
     cudaError_t e = fn(a, grid, threads, smem, stream);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "kernel launch");
+    if (ring_slot >= 0) {
+        e = cudaEventRecord(ctx->counter_ev[ring_slot], stream);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "work counter event");
+        ctx->counter_used[ring_slot] = true;
+    }
     return GF2X_OK;
 }
 

@@ -15,7 +15,7 @@ reconstruction is the sum of the pair/single terms of Alg. 1-3 written for
 any k, and the division by x+1 is the multiplication by
 sum_{i<d/w} X^{wi} mod X^d of Sec. 3.2.  It checks every exactness claim on
 the way (low w bits zero before /x, zero remainder after /(x+1)) and counts
-word products like Table tab:compKarat.  It is NOT the oracle: tests compare
+word products like the Karatsuba-variants complexity table of Sec. 2.1.  It is NOT the oracle: tests compare
 it against oracle/ and the GPU path implements the same algebra in CUDA.
 """
 from __future__ import annotations

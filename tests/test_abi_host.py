@@ -175,7 +175,7 @@ def test_seq_top_reduces_shared_memory():
 
 
 def test_paper_hqc_plans_through_the_abi():
-    """tab:NRperfs: hqc-128 at 18048 bits (Toom3Karat3, w=64) and hqc-256 at
+    """The HQC multiplication timing table of Sec. 4: hqc-128 at 18048 bits (Toom3Karat3, w=64) and hqc-256 at
     58368 bits (Toom3Karat5, w=512)."""
     a = gf2x.plan_info(17669, "T2.K3.K2.K2.K2/8")
     assert 32 * a["top_words"] == 18048 and a["nleaves"] == 5 * 6 * 27

@@ -1,7 +1,7 @@
 """CPU checks of the recursion algebra (Karatsuba k-way, word-aligned Toom-3).
 
 The model in plan_sim.py is pinned to the paper (worked example, printed
-sizes, M * M^-1 = I, Table tab:compKarat counts) and then compared with the
+sizes, M * M^-1 = I, the counts of the Karatsuba-variants complexity table of Sec. 2.1) and then compared with the
 oracle on random operands.
 """
 import json
@@ -83,7 +83,7 @@ def test_paper_sizes_follow_size_rule():
 
 @pytest.mark.parametrize("r", [1, 2, 3, 4, 5])
 def test_table_compkarat_clmul_counts(r):
-    """Table tab:compKarat: KaratRec t^lg3, Karat3 6 (t/3)^lg3, Karat5 15 (t/5)^lg3
+    """The Karatsuba-variants complexity table of Sec. 2.1: KaratRec t^lg3, Karat3 6 (t/3)^lg3, Karat5 15 (t/5)^lg3
     64-bit word products, with 64-bit leaves (S = 2 words of 32 bits)."""
     t = 2 ** r
     for top, expect in ((["K2"] * r, 3 ** r), (["K3"] + ["K2"] * r, 6 * 3 ** r), (["K5"] + ["K2"] * r, 15 * 3 ** r)):

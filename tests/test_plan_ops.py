@@ -2,7 +2,7 @@
 library's gf2x_plan_info.ops_full) against a second derivation in
 tests/plan_sim.py, for the benchmark plans and a spread of others, and the
 leaf products' useful AND-XOR count against the word products of Table
-tab:compKarat (clmul64 x 64 x 64 bit products / 32 per 32-bit operation)."""
+the Karatsuba-variants complexity table of Sec. 2.1 (clmul64 x 64 x 64 bit products / 32 per 32-bit operation)."""
 import pytest
 
 from paper_2201_10473_gb300 import autotune, gf2x
