@@ -770,10 +770,10 @@ def run_c4(device):
     bs = wl.sparse_operands(wk.seed, n, 131, count)
     da, db, dbs = _dev(a), _dev(b), _dev(bs)
     out = torch.empty((count, wl.limbs(n)), dtype=torch.int64, device="cuda")
-    ms_dense = _time_calls(lambda: ctx.mul_strided(da, db, n, True, out=out, persistent=True), 5, 2)
+    ms_dense = _time_calls(lambda: ctx.mul_strided(da, db, n, True, out=out), 5, 2)
     sample = np.arange(0, count, 2048)
     ok = bool(np.array_equal(_host(out)[sample], oracle.mul_batch(a[sample], b[sample], n, reduce=True)))
-    ms_sparse = _time_calls(lambda: ctx.mul_strided(da, dbs, n, True, out=out, persistent=True), 5, 2)
+    ms_sparse = _time_calls(lambda: ctx.mul_strided(da, dbs, n, True, out=out), 5, 2)
     ok &= bool(np.array_equal(_host(out)[sample], oracle.mul_batch(a[sample], bs[sample], n, reduce=True)))
     plan = ctx.get_plan(n)
     ctx.close()
