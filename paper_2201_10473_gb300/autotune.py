@@ -286,6 +286,7 @@ PACKAGED_SINGLE_LOG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "
 
 # top plans of the exhaustive log re-measured in the one-CTA-per-product
 # launch form (--launch cta), batches 2048, 4096 and 8192 of the six serving sizes
+# and an exhaustive search (split plans included) of 12323 at batch 256
 PACKAGED_CTA_LOG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans", "gb300_timing_log_cta.jsonl.gz")
 
 
