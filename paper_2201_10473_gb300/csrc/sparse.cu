@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(32 * kSparseWarps, MINB) sparse_mulmod_kernel(
 }
 
 // The compiled shapes: R result registers per lane, register offsets up to
-// QH, CTAs per SM the register budget allows.  The first eight keep D's
+// QH, CTAs per SM the register budget allows.  The first seven keep D's
 // whole window in registers (QH = R - 1 covers every offset of the n they
 // serve); the last three take the top bits of q in shared memory first.
 struct Variant {
