@@ -650,7 +650,8 @@ def run_c3(device):
     measured_sets = autotune.mixed_plan_sets(log, weights, 2048, top=3)
     model = costmodel.CostModel(seed=0)
     model.fit(costmodel.training_records(log), steps=3000, seed=0)
-    model_sets = autotune.model_mixed_plan_sets(model, weights, 2048, top=6)
+    model_top = 10   # as many as the per-size guided search measures
+    model_sets = autotune.model_mixed_plan_sets(model, weights, 2048, top=model_top)
     timed = []
     for origin, sets in (("log", measured_sets), ("model", model_sets)):
         for plans in sets:
@@ -748,6 +749,7 @@ def run_c3(device):
             "model_proposed_best_mults_per_s": total / (best_model[0] * 1e-3),
             "log_best_mults_per_s": total / (best_log[0] * 1e-3),
             "model_regret_vs_measured_log": model_regret,
+            "model_sets_measured": model_top,
             "plain_mults_per_s": total / (ms_plain * 1e-3),
             "per_size_launches_mults_per_s": total / (ms_grouped * 1e-3),
             "one_graph_concurrent_per_size_kernels_mults_per_s": total / (ms_graph * 1e-3),
