@@ -81,11 +81,15 @@ def test_plain_baseline_serves_everything():
         ctx.close()
 
 
-def test_size_aware_server_identical_alone_and_in_the_mix():
+@pytest.mark.parametrize("persistent", [True, False])
+def test_size_aware_server_identical_alone_and_in_the_mix(persistent):
+    """Both launch forms of the size-aware server: persistent CTAs taking the
+    item slots from a counter, and one CTA per item slot."""
     from paper_2201_10473_gb300 import Context, autotune, serve
     plans = autotune.best_plans(autotune.packaged_log(), SIZES, 512, allow_split=False)
     assert set(plans) == set(SIZES)
-    srv = serve.SizeAwareServer(plans, serve.default_budget(SIZES, 300), max_batch=256, streams_per_size=2)
+    srv = serve.SizeAwareServer(plans, serve.default_budget(SIZES, 300), max_batch=256, streams_per_size=2,
+                                persistent=persistent)
     ctx = Context(0)
     try:
         count = 1500
