@@ -282,17 +282,22 @@ gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, size_t count
  * the copies overlap the products (pageable memory works, with copies that
  * do not overlap).  The batch runs in up to four chunks through two sets of
  * device buffers owned by the context: while one chunk is multiplied (a
- * persistent launch on `stream`), the next chunk's operands are copied in
- * and the previous chunk's results copied out, on two copy streams of the
- * context ordered by events.
- *  - Ordering: the products wait for all work already enqueued on
- *    `stream`, and so do the operand copies unless flags has
- *    GF2X_HOST_INPUTS_READY (a and b are final at the call: their copies may
- *    then overlap earlier work, e.g. the previous call's last products).  A
- *    device buffer set is reused only after its previous product and result
- *    copy, whichever call (and stream) made them.  `stream` waits for the
- *    last result copy: synchronize it before reading `out`; the caller must
- *    not change a or b, nor read out, until then.
+ * persistent launch on one of two compute streams of the context, one per
+ * buffer set, so that a chunk's launch can fill the SMs the other's last
+ * round leaves idle), the next chunk's operands are copied in and the
+ * previous chunk's results copied out, on two copy streams of the context,
+ * all ordered by events.
+ *  - Ordering: without GF2X_HOST_INPUTS_READY the operand copies wait for
+ *    all work already enqueued on `stream`, and the products and result
+ *    copies wait for the operand copies, so the whole call follows that
+ *    work.  With GF2X_HOST_INPUTS_READY nothing of the call waits for
+ *    `stream`: a and b must be final and `out` unused by earlier work at
+ *    the call, and the copies and products may overlap that work (e.g. the
+ *    previous call's last products).  A device buffer set is reused only
+ *    after its previous product and result copy, whichever call (and
+ *    stream) made them.  `stream` waits for the last result copy:
+ *    synchronize it before reading `out`; the caller must not change a or
+ *    b, nor read out, until then.
  *  - Rows: only the ceil(n/64) operand limbs of each row are read and only
  *    the result limbs written; limbs between rows (strides above the sizes)
  *    are left untouched.

@@ -422,8 +422,8 @@ class Context:
         library copies chunks in, multiplies and copies results out on its own
         streams; `stream` waits for the last copy.  Keep a, b and out alive and
         unchanged until `stream` has been synchronized.  inputs_ready: a and b
-        are final now, so their copies need not wait for earlier work on
-        `stream`."""
+        are final now and out is unused by earlier work, so nothing of the
+        call waits for earlier work on `stream`."""
         if a.dim() != 2 or a.shape != b.shape:
             raise ValueError("a and b must be equal-shaped 2-D tensors")
         for t, name in ((a, "a"), (b, "b")):
