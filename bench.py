@@ -579,7 +579,7 @@ def run_c1(device):
     ms = _time_calls(plain, 3, 1)
     ok = bool(np.array_equal(_host(out), oracle.mul_batch(a, b, n, reduce=False)))
     out.zero_()
-    ms_b = _time_calls(lambda: ctx.mul_strided(da, db, n, False, out=out, persistent=True), 10, 3)
+    ms_b = _time_calls(lambda: ctx.mul_strided(da, db, n, False, out=out), 10, 3)
     ok &= bool(np.array_equal(_host(out), oracle.mul_batch(a, b, n, reduce=False)))
     plain_plan = cp.get_plan(n)
     ctx.close()
@@ -691,11 +691,12 @@ def run_c3(device):
     cp.close()
     ctx.close()
     # per-size launches with each size's own tuned plan, one after the other
+    # (one CTA per product)
     ctx2 = Context(device, batch_hint=2048)
 
     def grouped():
         for n in weights:
-            ctx2.mul_strided(reqs.a[int(n)], reqs.b[int(n)], int(n), True, out=outs[int(n)], persistent=True)
+            ctx2.mul_strided(reqs.a[int(n)], reqs.b[int(n)], int(n), True, out=outs[int(n)])
     ms_grouped = _time_calls(grouped, 10, 3)
     ctx2.close()
     # ONE graph launch: the per-size tuned kernels (split plans included) on
@@ -789,7 +790,8 @@ def run_c4(device):
 def run_shared(device):
     """One public key h times many vectors at n = 17669 (reduced mod X^n - 1),
     shared-operand launch against the unshared launch with h copied into every
-    row; 4096 products per launch, 8 rotating input sets (> L2)."""
+    row (one CTA per product) and the tensor-core circulant GEMM; 4096
+    products per launch, 8 rotating input sets (> L2)."""
     import torch
 
     import oracle
@@ -806,7 +808,7 @@ def run_shared(device):
     def call(a_of):
         r = it[0] % R
         it[0] += 1
-        ctx.mul_strided(a_of(r), dv[r], n, True, out=out, persistent=True)
+        ctx.mul_strided(a_of(r), dv[r], n, True, out=out)
     def call_tc():
         r = it[0] % R
         it[0] += 1
@@ -875,7 +877,7 @@ def run_unbalanced(device):
     """2048 full products of a 57637-bit a and a 17669-bit b through the
     unbalanced entry (four 17728-bit chunk products and an overlap-add, as
     the op model picks), against the equal-size 57637 product of the
-    zero-extended b; 4 rotating input sets (> L2)."""
+    zero-extended b (one CTA per product); 4 rotating input sets (> L2)."""
     import torch
 
     import oracle
@@ -902,7 +904,7 @@ def run_unbalanced(device):
     def padded():
         _, _, da, _, dbz = sets[it[0] % R]
         it[0] += 1
-        ctx.mul_strided(da, dbz, na, False, out=full, persistent=True)
+        ctx.mul_strided(da, dbz, na, False, out=full)
     rates = {}
     for rep in range(2):
         for name, fn in (("unbalanced", unbalanced), ("padded", padded)):
@@ -928,7 +930,8 @@ def run_unbalanced(device):
 def run_sparse(device):
     """Constant-time sparse x dense products mod X^n - 1 (HQC shapes: n =
     17669 with weight 75, n = 57637 with weight 131) against the dense path
-    on the same operands (the sparse operand expanded to n bits)."""
+    on the same operands (the sparse operand expanded to n bits; one CTA per
+    product)."""
     import torch
 
     import oracle
@@ -949,7 +952,7 @@ def run_sparse(device):
             it[0] += 1
 
         def dense():
-            ctx.mul_strided(da[it[0] % R], dden, n, True, out=out, persistent=True)
+            ctx.mul_strided(da[it[0] % R], dden, n, True, out=out)
             it[0] += 1
         rates = {}
         for rep in range(2):
@@ -972,7 +975,7 @@ def run_sparse(device):
 
 def run_toom4(device):
     """Toom-4 and Toom-5 top levels against the regular path (the tuned or
-    default plan) at 57637, 100000 and 131072 bits, 512 products mod X^n - 1
+    default plan, one CTA per product) at 57637, 100000 and 131072 bits, 512 products mod X^n - 1
     each."""
     import torch
 
@@ -989,7 +992,7 @@ def run_toom4(device):
         for rep in range(2):
             for name, fn in (("toom4", lambda: ctx.mul_toom4(da, db, n, True, out=out)),
                              ("toom5", lambda: ctx.mul_toom5(da, db, n, True, out=out)),
-                             ("regular", lambda: ctx.mul_strided(da, db, n, True, out=out, persistent=True))):
+                             ("regular", lambda: ctx.mul_strided(da, db, n, True, out=out))):
                 ms = _time_calls(fn, 5, 2)
                 rates.setdefault(name, []).append(count / (ms * 1e-3))
         ok = True

@@ -702,7 +702,10 @@ static gf2x_status run_split_on(gf2x_ctx *ctx, uint32_t top_slot, uint32_t *ws, 
         ca.count = (uint32_t)(k * nch);
         ca.mode = kItemsStrided;
         ca.err = ctx->err_dev;
-        gf2x_status st = launch(ctx, ca, C.S, C.threads, 4ull * C.smem_words, k * nch, persistent, stream);
+        // persistent: the children are taken in order from a counter, as the
+        // products of an unsplit plan are
+        gf2x_status st = launch(ctx, ca, C.S, C.threads, 4ull * C.smem_words, k * nch, persistent, stream,
+                                persistent);
         if (st != GF2X_OK)
             return st;
         e = launch_split_interp(ta, ws, tgrid, top_threads, top_smem, stream);
