@@ -283,10 +283,10 @@ gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, size_t count
  * layout, strides and flags as gf2x_mul_strided; page-locked memory lets
  * the copies overlap the products (pageable memory works, with copies that
  * do not overlap).  The batch runs in up to four chunks through two sets of
- * device buffers owned by the context: while one chunk is multiplied (a
- * persistent launch on one of two compute streams of the context, one per
+ * device buffers owned by the context: while one chunk is multiplied (one
+ * CTA per product, on one of two compute streams of the context, one per
  * buffer set, so that a chunk's launch can fill the SMs the other's last
- * round leaves idle), the next chunk's operands are copied in and the
+ * wave leaves idle), the next chunk's operands are copied in and the
  * previous chunk's results copied out, on two copy streams of the context,
  * all ordered by events.
  *  - Ordering: without GF2X_HOST_INPUTS_READY the operand copies wait for

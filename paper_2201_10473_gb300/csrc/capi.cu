@@ -1006,7 +1006,9 @@ extern "C" gf2x_status gf2x_mul_unbalanced(gf2x_ctx *ctx, uint64_t *out, const u
             return cuda_fail(ctx, e, "operand padding launch");
         if (g * chunks > 0xffffffffull)
             return fail(ctx, GF2X_EINVAL, "batch too large");
-        gf2x_status st = strided_on_slot(ctx, slot, P, A, B, g * chunks, Ld, Wp, 0u, GF2X_BATCH_PERSISTENT, s);
+        // one CTA per chunk product: 1.95 against 1.84 M/s for persistent
+        // launches at 2048 x (57637 x 17669)
+        gf2x_status st = strided_on_slot(ctx, slot, P, A, B, g * chunks, Ld, Wp, 0u, 0u, s);
         if (st != GF2X_OK)
             return st;
         e = launch_overlap_add(out + c0 * stride_out, stride_out, Lu, P, Wp, g, chunks, step, ctx->sm_count, s);
@@ -1308,7 +1310,9 @@ extern "C" gf2x_status gf2x_mul_strided_host(gf2x_ctx *ctx, uint64_t *out, const
             e = cudaStreamWaitEvent(hp.comp[p], hp.out[p], 0);
         if (e != cudaSuccess)
             return cuda_fail(ctx, e, "host pipeline copy in");
-        st = gf2x_mul_strided(ctx, dout, da, db, n, k, L, Lo, flags, GF2X_BATCH_PERSISTENT, hp.comp[p]);
+        // one CTA per product (end to end 8.29 against 8.27 M/s for persistent
+        // launches at 4096 x 17669, 1.11 against 1.06 at 2048 x 57637)
+        st = gf2x_mul_strided(ctx, dout, da, db, n, k, L, Lo, flags, 0u, hp.comp[p]);
         if (st != GF2X_OK)
             return st;
         e = cudaEventRecord(hp.done[p], hp.comp[p]);
