@@ -1459,7 +1459,7 @@ extern "C" gf2x_status gf2x_mul_batched(gf2x_ctx *ctx, const gf2x_item *items, s
             return ctx->plans_host[dv[x].plan].n > ctx->plans_host[dv[y].plan].n;
         return false;
     });
-    Staging *stg;
+    Staging *stg = nullptr;
     gf2x_status st = take_staging(ctx, count, &stg);
     if (st != GF2X_OK)
         return st;

@@ -37,7 +37,10 @@ def main():
     p.add_argument("--count", type=int, default=4096)
     p.add_argument("--samples", type=int, default=200)
     p.add_argument("--ncu", action="store_true")
+    p.add_argument("--launch", choices=("cta", "persistent"), default="cta",
+                   help="one CTA per product (the default form) or persistent CTAs taking products from a counter")
     a = p.parse_args()
+    persistent = a.launch == "persistent"
     n, count = a.n, a.count
     L = wl.limbs(n)
     ctx = Context(0, batch_hint=count)
@@ -51,14 +54,14 @@ def main():
     out = torch.empty((count, L), dtype=torch.int64, device="cuda")
     if a.ncu:
         for k, (x, y) in dev.items():
-            ctx.mul_strided(x, y, n, True, out=out, persistent=True)
+            ctx.mul_strided(x, y, n, True, out=out, persistent=persistent)
             torch.cuda.synchronize()
             print(f"launched class {k}", flush=True)
         return
     times = {k: [] for k in dev}
     for _ in range(3):
         for x, y in dev.values():
-            ctx.mul_strided(x, y, n, True, out=out, persistent=True)
+            ctx.mul_strided(x, y, n, True, out=out, persistent=persistent)
     torch.cuda.synchronize()
     order = list(dev)
     for s in range(a.samples):
@@ -66,11 +69,11 @@ def main():
             x, y = dev[k]
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            ctx.mul_strided(x, y, n, True, out=out, persistent=True)
+            ctx.mul_strided(x, y, n, True, out=out, persistent=persistent)
             e1.record()
             torch.cuda.synchronize()
             times[k].append(e0.elapsed_time(e1))
-    print(f"n={n} count={count} plan={ctx.get_plan(n)} samples={a.samples}")
+    print(f"n={n} count={count} plan={ctx.get_plan(n)} launch={a.launch} samples={a.samples}")
     for k, t in times.items():
         print(f"{k:10s} median {np.median(t):.4f} ms  mean {np.mean(t):.4f}  sd {np.std(t):.4f}  "
               f"Welch t vs dense {welch_t(t, times['dense']):+.2f}")

@@ -18,24 +18,27 @@ from gpu_util import to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 
-def _median_launch_ms(ctx, da, db, n, out, reps=7, inner=10):
+def _median_launch_ms(ctx, da, db, n, out, persistent, reps=7, inner=10):
     for _ in range(3):
-        ctx.mul_strided(da, db, n, True, out=out, persistent=True)
+        ctx.mul_strided(da, db, n, True, out=out, persistent=persistent)
     times = []
     for _ in range(reps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(inner):
-            ctx.mul_strided(da, db, n, True, out=out, persistent=True)
+            ctx.mul_strided(da, db, n, True, out=out, persistent=persistent)
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / inner)
     return float(np.median(times))
 
 
+@pytest.mark.parametrize("persistent", [False, True])
 @pytest.mark.parametrize("n", [17669, 57637])
-def test_launch_time_independent_of_operand_bits(n):
+def test_launch_time_independent_of_operand_bits(n, persistent):
+    """Both launch forms: one CTA per product, and persistent CTAs taking
+    the products from a counter."""
     from paper_2201_10473_gb300 import Context
     ctx = Context(0)
     try:
@@ -53,7 +56,7 @@ def test_launch_time_independent_of_operand_bits(n):
         dev = {name: (to_dev(a), to_dev(b)) for name, (a, b) in classes.items()}
         sample = np.arange(0, count, 512)
         for name, (da, db) in dev.items():
-            ctx.mul_strided(da, db, n, True, out=out, persistent=True)
+            ctx.mul_strided(da, db, n, True, out=out, persistent=persistent)
             a, b = classes[name]
             assert np.array_equal(to_host(out)[sample], oracle.mul_batch(a[sample], b[sample], n, reduce=True)), name
         # a second of launches first, so that no class is timed while the
@@ -62,12 +65,12 @@ def test_launch_time_independent_of_operand_bits(n):
         da, db = dev["dense"]
         t_end = time.time() + 1.0
         while time.time() < t_end:
-            ctx.mul_strided(da, db, n, True, out=out, persistent=True)
+            ctx.mul_strided(da, db, n, True, out=out, persistent=persistent)
             torch.cuda.synchronize()
         rounds = {name: [] for name in dev}
         for _ in range(3):
             for name, (da, db) in dev.items():
-                rounds[name].append(_median_launch_ms(ctx, da, db, n, out))
+                rounds[name].append(_median_launch_ms(ctx, da, db, n, out, persistent))
         ms = {name: min(t) for name, t in rounds.items()}
         spread = max(ms.values()) / min(ms.values())
         assert spread < 1.05, ms
