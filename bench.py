@@ -761,7 +761,8 @@ def run_c3(device):
 
 
 def run_c4(device):
-    """16384 products at n=57637: dense, and sparse (weight 131) x dense through the same path."""
+    """16384 products at n=57637: dense, and sparse (weight 131) x dense through
+    the same path and through the sparse x dense kernel (positions)."""
     import torch
 
     import oracle
@@ -778,12 +779,22 @@ def run_c4(device):
     ok = bool(np.array_equal(_host(out)[sample], oracle.mul_batch(a[sample], b[sample], n, reduce=True)))
     ms_sparse = _time_calls(lambda: ctx.mul_strided(da, dbs, n, True, out=out), 5, 2)
     ok &= bool(np.array_equal(_host(out)[sample], oracle.mul_batch(a[sample], bs[sample], n, reduce=True)))
+    # the same sparse operands given by their 131 positions, through the
+    # constant-time sparse x dense kernel
+    pos = np.stack([np.flatnonzero(np.unpackbits(r.view(np.uint8), bitorder="little"))[:131] for r in bs])
+    dpos = torch.from_numpy(pos.astype(np.int32)).cuda()
+    out.zero_()
+    ms_kernel = _time_calls(lambda: ctx.mulmod_sparse(da, dpos, n, out=out), 5, 2)
+    ok &= bool(np.array_equal(_host(out)[sample], oracle.mul_batch(a[sample], bs[sample], n, reduce=True)))
     plan = ctx.get_plan(n)
     ctx.close()
     return {"workload": wk.name, "products": count, "plan": plan,
             "dense_mults_per_s": count / (ms_dense * 1e-3), "sparse131_mults_per_s": count / (ms_sparse * 1e-3),
             "sparse_over_dense_time": ms_sparse / ms_dense,
-            "note": "sparse operand goes through the dense constant-time path (same work, same time)",
+            "sparse131_positions_kernel_mults_per_s": count / (ms_kernel * 1e-3),
+            "note": "dense path: the sparse operand goes through the dense constant-time path (same work, same "
+                    "time); positions kernel: gf2x_mulmod_sparse on the same operands",
+            "launch": "one CTA per product",
             "sample_checked_against_oracle": ok}
 
 
