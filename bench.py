@@ -427,6 +427,43 @@ def run_ours(args, w):
                               oracle.mul_batch(host_a[sample], host_b[sample], n, reduce=reduce)):
             raise SystemExit("bench: persistent-launch results differ from the oracle")
 
+    # ---- consecutive steps on two streams without a join between them: the
+    # next batch's CTAs start on the SMs that the previous batch's last wave
+    # leaves idle (what the host-buffer pipeline does across its chunks and
+    # calls); same inputs, plan and launch, each stream its own result buffer
+    Ko = max(4, min(K, 400))
+    out2 = torch.empty_like(out)
+    two = [torch.cuda.Stream(device=local), torch.cuda.Stream(device=local)]
+
+    def overlapped(k):
+        a, b = sets[k % R]
+        st = two[k % 2]
+        ctx.mul_strided(a, b, n, reduce, out=out if k % 2 == 0 else out2, stream=st)
+
+    torch.cuda.synchronize()
+    o0 = torch.cuda.Event(enable_timing=True)
+    o1 = torch.cuda.Event(enable_timing=True)
+    o0.record(stream)
+    for st in two:
+        st.wait_stream(stream)
+    for k in range(Ko):
+        overlapped(k)
+    for st in two:
+        stream.wait_stream(st)
+    o1.record(stream)
+    torch.cuda.synchronize()
+    ov_ms = shard.max_over_ranks(o0.elapsed_time(o1), device="cuda")
+    overlapped_form = {"mults_per_s": shard.whole_job_rate(batch * Ko, world, ov_ms * 1e-3), "steps": Ko,
+                       "form": "consecutive batches alternate between two streams, one launch of one CTA per "
+                               "product each, no join between batches"}
+    if rank == 0 and import_oracle_ok:
+        import oracle
+        sample = np.arange(0, batch, max(1, batch // 16))
+        for o in (out, out2):
+            if not np.array_equal(o.cpu().numpy().view(np.uint64)[sample],
+                                  oracle.mul_batch(host_a[sample], host_b[sample], n, reduce=reduce)):
+                raise SystemExit("bench: overlapped-step results differ from the oracle")
+
     # ---- plain form: one launch of one CTA per product, with the plan tuned
     # for a single product per launch
     plain = None
@@ -514,6 +551,7 @@ def run_ours(args, w):
         "roofline": roof,
         "cpu_baseline": cpu,
         "persistent_launch": persistent_form,
+        "overlapped_steps": overlapped_form,
         "plain": plain,
         "batched_over_plain": (value / world / plain["value"]) if plain else None,
         "clocks": clk,
