@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="hqc128")
     p.add_argument("--no-plain", action="store_true", help="skip the plain one-launch-per-product measurement")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle cpu_baseline sample")
-    p.add_argument("--no-extras", action="store_true", help="skip the other workloads (C1, C3, C4, shared key, unbalanced, sparse, Toom-4, C5)")
+    p.add_argument("--no-extras", action="store_true", help="skip the other workloads (C1, C3, C4, the three HQC sizes, shared key, unbalanced, sparse, Toom-4, C5)")
     p.add_argument("--serving-requests", type=int, default=200000)
     p.add_argument("--plan", default=None, help="plan spec for the main workload (default: the tuned database)")
     p.add_argument("--only-extra", default=None, choices=sorted(EXTRAS),
@@ -836,6 +836,54 @@ def run_c4(device):
             "sample_checked_against_oracle": ok}
 
 
+def run_hqc_sizes(device):
+    """The three HQC sizes of the metric (17669, 35851, 57637 mod X^n - 1):
+    the batched launch (tuned plan, one CTA per product; 4096, 2048 and 2048
+    products, rotating copies of the inputs that together exceed L2) against
+    one plain launch per product with the single-product plan (256
+    launches)."""
+    import torch
+
+    import oracle
+    from paper_2201_10473_gb300 import Context, autotune
+    res = {"workload": "hqc-sizes-mulmod"}
+    for key, n, count in ((2, 17669, 4096), (3, 35851, 2048), (4, 57637, 2048)):
+        ctx = Context(device, batch_hint=count)
+        cp = Context(device, plan_db=None)
+        single = autotune.single_product_plans([n]).get(n)
+        if single:
+            cp.set_plan(n, single)
+        a, b = wl.dense_pair(wl.BASE_SEED + key, n, count)
+        R = max(2, int(np.ceil(160e6 / (2 * a.nbytes))))
+        sets = [(_dev(a), _dev(b)) for _ in range(R)]
+        out = torch.empty((count, wl.limbs(n)), dtype=torch.int64, device="cuda")
+        it = [0]
+
+        def batched():
+            da, db = sets[it[0] % R]
+            it[0] += 1
+            ctx.mul_strided(da, db, n, True, out=out)
+        ms_b = _time_calls(batched, 20, 3)
+        s = np.arange(0, count, count // 8)
+        ok = bool(np.array_equal(_host(out)[s], oracle.mul_batch(a[s], b[s], n, reduce=True)))
+        m = 256
+        da, db = sets[0]
+
+        def plain():
+            for p in range(m):
+                cp.mulmod(da[p], db[p], n, out=out[p])
+        out.zero_()
+        ms_p = _time_calls(plain, 2, 1)
+        ok &= bool(np.array_equal(_host(out)[:m:37], oracle.mul_batch(a[:m:37], b[:m:37], n, reduce=True)))
+        res[f"n{n}"] = {"products": count, "plan": ctx.get_plan(n), "mults_per_s": count / (ms_b * 1e-3),
+                        "ns_per_mult": ms_b * 1e6 / count, "plain_plan": cp.get_plan(n),
+                        "plain_mults_per_s": m / (ms_p * 1e-3), "batched_over_plain": (count / ms_b) / (m / ms_p),
+                        "sample_checked_against_oracle": ok}
+        ctx.close()
+        cp.close()
+    return res
+
+
 def run_shared(device):
     """One public key h times many vectors at n = 17669 (reduced mod X^n - 1),
     shared-operand launch against the unshared launch with h copied into every
@@ -1141,12 +1189,13 @@ def run_c5(device, requests):
     return out
 
 
-EXTRAS = ("c1", "c3", "c4", "shared_key", "unbalanced", "sparse_ct", "toom4", "c5")
+EXTRAS = ("c1", "c3", "c4", "hqc_sizes", "shared_key", "unbalanced", "sparse_ct", "toom4", "c5")
 
 
 def run_extras(args, device, only=None):
     res = {}
     for name, fn in (("c1", lambda: run_c1(device)), ("c3", lambda: run_c3(device)), ("c4", lambda: run_c4(device)),
+                     ("hqc_sizes", lambda: run_hqc_sizes(device)),
                      ("shared_key", lambda: run_shared(device)), ("unbalanced", lambda: run_unbalanced(device)),
                      ("sparse_ct", lambda: run_sparse(device)), ("toom4", lambda: run_toom4(device)),
                      ("c5", lambda: run_c5(device, args.serving_requests))):
