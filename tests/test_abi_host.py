@@ -72,6 +72,40 @@ def test_entries_reject_a_null_context_without_a_gpu():
     assert L.gf2x_sparse_info_get(100, None) == 1
 
 
+def _prototypes():
+    text = open(os.path.join(ROOT, "include", "gf2x_gb300.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    for ret, name, params in re.findall(r"\b(gf2x_status|const char \*|void|uint32_t)\s*(gf2x_[a-z0-9_]+)\s*\(([^)]*)\)\s*;",
+                                        text):
+        yield ret, name, [p.strip() for p in params.split(",")]
+
+
+def test_every_context_entry_rejects_a_null_context_without_a_gpu():
+    """Every entry point whose first argument is a context returns
+    GF2X_EINVAL for a null one before it touches any other argument or the
+    GPU (the header's error rule); destroy(NULL) is a no-op."""
+    import ctypes
+    L = gf2x.lib()
+    checked = 0
+    for ret, name, params in _prototypes():
+        if params[0] != "gf2x_ctx *ctx":
+            continue
+        fn = getattr(L, name)
+        if ret == "gf2x_status":
+            types = getattr(fn, "argtypes", None) or [None] * len(params)
+            args = [None if t is None or issubclass(t, (ctypes.c_void_p, ctypes.c_char_p, ctypes._Pointer)) else 0
+                    for t in types]
+            assert fn(*args) == 1, name     # restype as the binding declared it (an int status)
+            checked += 1
+        elif ret == "void":
+            fn.restype = None
+            fn(None)
+        else:
+            fn.restype = ctypes.c_char_p
+            assert fn(None)
+    assert checked >= 20
+
+
 def test_status_strings_and_version():
     L = gf2x.lib()
     assert L.gf2x_status_str(0) == b"ok"
