@@ -228,7 +228,7 @@ gf2x_status gf2x_mulmod_xn1(gf2x_ctx *ctx, uint64_t *r, const uint64_t *a, const
  * memset on `stream`; with a split plan, its child products are taken
  * from such a counter; without the flag, one CTA per product (per child),
  * which measured faster on GB300 when the batch is not a multiple of the
- * grid, e.g. 7.88 against 7.74 M products/s at 4096 x 17669), and
+ * grid, e.g. 7.93 against 7.73 M products/s at 4096 x 17669), and
  * GF2X_BATCH_SHARED_A, with which every product
  * reads the same a (its ceil(n/64) limbs; only b advances by stride_in),
  * as when one public-key polynomial of the HQC/BIKE operations of Sec. 1
